@@ -1,0 +1,353 @@
+"""Pins of the CPU oracle's building blocks against closed forms and limits that
+the paper and the mathematics fix (no GPU).
+
+Every check compares the oracle with something other than itself: exact
+Gauss-Hermite quadrature of Maxwellian moments, the moment coefficients the paper
+prints in Step 6 (Eqs. solve_erot, solve_qtr, solve_qrot), the free-molecular and
+continuum limits stated after Eq. flux_solve_phi, eigenvalues of the Euler flux
+Jacobian, exactness of least squares for linear data, and telescoping of face
+fluxes."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_10846_gb300 import inputs as I
+from tests import workloads as TW
+
+R = I.R_GAS
+STATE = dict(rho=1.3, U=(0.3, -0.2, 0.1), Ttr=1.2, Trot=0.8,
+             qtr=(0.05, -0.03, 0.02), qrot=(0.01, 0.02, -0.015))
+
+
+def _state(**kw):
+    d = dict(STATE)
+    d.update(kw)
+    T = (3 * d["Ttr"] + 2 * d["Trot"]) / 5          # Eq. f_solve_Energy with K_tr=3, K_rot=2
+    return O.make_state(d["rho"], d["U"], T, d["Ttr"], d["Trot"], d["qtr"], d["qrot"]), T
+
+
+def _grid(n, U, T):
+    d = I.gauss_hermite_dvs(n, RT=R * T, centre=U)
+    return d.u, d.w
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300)
+
+
+P = I.Params(Z_rot=3.5)
+
+
+# ---------------------------------------------------------------------------------
+# P1: moments of the four Rykov pieces, exact Gauss-Hermite quadrature
+# ---------------------------------------------------------------------------------
+def test_rykov_translational_pieces_moments():
+    s, T = _state()
+    U, rho, Ttr, Trot = np.array(STATE["U"]), STATE["rho"], STATE["Ttr"], STATE["Trot"]
+    qtr, qrot = np.array(STATE["qtr"]), np.array(STATE["qrot"])
+    u, w = _grid(12, U, Ttr)             # exact for polynomials x Maxwellian(T_tr)
+    Gtr, Grot, Htr, Hrot = O.equilibrium_parts(P, s, u)
+    c = u - U
+    c2 = (c * c).sum(1)
+    assert abs(w @ Gtr - rho) < 1e-13
+    assert _rel((w * Gtr) @ u, rho * U) < 1e-13
+    assert abs(w @ (0.5 * c2 * Gtr) - 1.5 * rho * R * Ttr) < 1e-13
+    assert _rel(0.5 * (w * c2 * Gtr) @ c, qtr / 3.0) < 1e-12
+    stress = np.einsum("k,ki,kj->ij", w * Gtr, c, c)
+    assert _rel(stress, rho * R * Ttr * np.eye(3)) < 1e-13
+    assert abs(w @ Htr - rho * R * Trot) < 1e-13
+    assert _rel((w * Htr) @ c, (1 - P.delta) * qrot) < 1e-12
+
+
+def test_rykov_rotational_pieces_moments():
+    s, T = _state()
+    U, rho = np.array(STATE["U"]), STATE["rho"]
+    qtr, qrot = np.array(STATE["qtr"]), np.array(STATE["qrot"])
+    u, w = _grid(12, U, T)
+    Gtr, Grot, Htr, Hrot = O.equilibrium_parts(P, s, u)
+    c = u - U
+    c2 = (c * c).sum(1)
+    assert abs(w @ Grot - rho) < 1e-13
+    assert abs(w @ (0.5 * c2 * Grot) - 1.5 * rho * R * T) < 1e-13
+    assert _rel(0.5 * (w * c2 * Grot) @ c, P.omega0 * qtr / 3.0) < 1e-12
+    assert abs(w @ Hrot - rho * R * T) < 1e-13
+    assert _rel((w * Hrot) @ c, P.omega1 * (1 - P.delta) * qrot) < 1e-12
+
+
+# ---------------------------------------------------------------------------------
+# P2/P3: moments of G*, R* reproduce the coefficients printed in Step 6 and the
+# collision invariants
+# ---------------------------------------------------------------------------------
+def test_equilibrium_moments_match_step6_coefficients():
+    s, T = _state()
+    U, rho, Ttr, Trot = np.array(STATE["U"]), STATE["rho"], STATE["Ttr"], STATE["Trot"]
+    qtr, qrot = np.array(STATE["qtr"]), np.array(STATE["qrot"])
+    u, w = _grid(28, U, 0.5 * (T + Ttr))
+    G, H = O.equilibrium(P, s, u)
+    c = u - U
+    c2 = (c * c).sum(1)
+    Z = P.Z_rot
+    rhoE = 0.5 * rho * U @ U + 2.5 * rho * R * T
+    assert abs(w @ G - rho) < 1e-12
+    assert _rel((w * G) @ u, rho * U) < 1e-12
+    assert abs(w @ (0.5 * (u * u).sum(1) * G + H) - rhoE) < 1e-12
+    # Eq. solve_erot: exact rotational energy of R*
+    assert abs(w @ H - rho * R * ((1 - 1 / Z) * Trot + T / Z)) < 1e-12
+    # Eq. solve_qtr / solve_qrot coefficients
+    assert _rel(0.5 * (w * c2 * G) @ c, qtr * (1 - (1 - P.omega0) / Z) / 3.0) < 1e-10
+    assert _rel((w * H) @ c, qrot * (1 - P.delta) * (1 - (1 - P.omega1) / Z)) < 1e-10
+
+
+def test_collision_conserves_mass_momentum_energy():
+    """For any distribution, the Rykov equilibrium built from its moments has the
+    same rho, rho U, rho E; the rotational row relaxes by (rho R T - rho E_rot)/Z."""
+    rng = np.random.default_rng(3)
+    u, w = _grid(16, np.zeros(3), 1.0)
+    M = np.exp(-(u * u).sum(1) / (2 * R)) / (2 * math.pi * R) ** 1.5
+    g = M * (1 + 0.2 * np.tanh(u @ rng.standard_normal(3)))
+    h = 0.6 * R * M * (1 + 0.1 * np.sin(u[:, 0]))
+    rho = w @ g
+    U = (w * g) @ u / rho
+    E = w @ (0.5 * (u * u).sum(1) * g + h)
+    Er = w @ h
+    ke = 0.5 * rho * U @ U
+    Ttr = (E - ke - Er) / (1.5 * rho * R)
+    Trot = Er / (rho * R)
+    T = (E - ke) / (2.5 * rho * R)
+    c = u - U
+    qtr = 0.5 * (w * (c * c).sum(1) * g) @ c
+    qrot = (w * h) @ c
+    s = O.make_state(rho, U, T, Ttr, Trot, qtr, qrot)
+    G, H = O.equilibrium(P, s, u)
+    d_rho = w @ (G - g)
+    d_mom = (w * (G - g)) @ u
+    d_E = w @ (0.5 * (u * u).sum(1) * (G - g) + (H - h))
+    d_rot = w @ (H - h)
+    assert abs(d_rho) < 1e-10 and np.abs(d_mom).max() < 1e-10 and abs(d_E) < 1e-10
+    assert abs(d_rot - (rho * R * T - Er) / P.Z_rot) < 1e-10
+
+
+# ---------------------------------------------------------------------------------
+# P7/P8: interface distribution limits (text after Eq. flux_solve_phi)
+# ---------------------------------------------------------------------------------
+def _face_input(n=14):
+    u, w = _grid(n, np.array([0.2, 0.1, 0.0]), 1.1)
+    c = u - np.array([0.25, 0.05, 0.0])
+    M = 1.2 * np.exp(-(c * c).sum(1) / (2 * R * 1.05)) / (2 * math.pi * R * 1.05) ** 1.5
+    g0 = M * (1 + 0.05 * c[:, 0] * ((c * c).sum(1) - 2.0))
+    h0 = R * 0.9 * M * (1 + 0.04 * c[:, 1])
+    return u, w, g0, h0
+
+
+def test_free_molecular_limit():
+    u, w, g0, h0 = _face_input()
+    p = I.Params(mu_ref=1e12)
+    st, gf, hf = O.interface(p, u, w, g0, h0, 0.01)
+    assert _rel(gf, g0) < 1e-10 and _rel(hf, h0) < 1e-10
+    # free transport: E_rot is the raw moment, q the raw heat flux
+    assert abs(st[0] * R * st[6] - w @ h0) < 1e-10
+    U = st[1:4]
+    c = u - U
+    assert _rel(st[8:11], 0.5 * (w * (c * c).sum(1) * g0) @ c) < 1e-8
+
+
+def test_continuum_limit_gives_euler_flux():
+    """tau << s: the face distribution is the Maxwellian of the face state with
+    T_rot = T and q = 0, and its DVS flux is the Euler flux G(W) of Eq.
+    implicit_mac_equ_euler_flux (exact on a Gauss-Hermite grid matched to it)."""
+    U = np.array([0.3, -0.1, 0.2])
+    T, rho = 1.3, 0.9
+    u, w = _grid(10, U, T)
+    c = u - U
+    M = rho * np.exp(-(c * c).sum(1) / (2 * R * T)) / (2 * math.pi * R * T) ** 1.5
+    g0, h0 = M, R * T * M
+    p = I.Params(mu_ref=1e-14)
+    st, gf, hf = O.interface(p, u, w, g0, h0, 0.01)
+    assert abs(st[6] - st[4]) < 1e-10                  # T_rot -> T
+    assert np.abs(st[8:14]).max() < 1e-10              # q -> 0
+    assert _rel(gf, M) < 1e-10 and _rel(hf, R * T * M) < 1e-10
+    n = np.array([0.6, 0.0, 0.8])
+    un = u @ n
+    flux = np.array([w @ (un * gf), *((w * un * gf) @ u),
+                     w @ (un * (0.5 * (u * u).sum(1) * gf + hf)), w @ (un * hf)])
+    W = np.array([rho, *(rho * U), 0.5 * rho * U @ U + 2.5 * rho * R * T, rho * R * T])
+    assert _rel(O.euler_flux(p, W, n), flux) < 1e-12
+
+
+def test_interface_state_is_self_consistent():
+    """The interface W and q of Eqs. halftime_solve_* are the moments of the face
+    distribution of Eq. flux_solve_phi built from them (the derivation behind the
+    denominators), up to quadrature error of the equilibrium moments."""
+    u, w, g0, h0 = _face_input(24)
+    p = I.Params(mu_ref=0.05)
+    for s in (0.003, 0.05, 0.4):
+        st, gf, hf = O.interface(p, u, w, g0, h0, s)
+        rho, U = st[0], st[1:4]
+        c = u - U
+        c2 = (c * c).sum(1)
+        assert abs(w @ gf - rho) < 1e-11
+        assert _rel((w * gf) @ u, rho * U) < 1e-11
+        assert abs(w @ hf - rho * R * st[6]) < 1e-9                    # E_rot
+        assert _rel(0.5 * (w * c2 * gf) @ c, st[8:11]) < 1e-7            # q_tr
+        assert _rel((w * hf) @ c, st[11:14]) < 1e-7                     # q_rot
+
+
+# ---------------------------------------------------------------------------------
+# Euler flux and spectral radius
+# ---------------------------------------------------------------------------------
+def test_euler_jacobian_spectral_radius():
+    p = I.Params()
+    W = np.array([1.1, 0.5, -0.3, 0.2, 3.1, 0.55])
+    n = np.array([1.0, 2.0, -2.0]) / 3.0
+    J = np.zeros((6, 6))
+    for j in range(6):
+        e = np.zeros(6)
+        e[j] = 1e-6
+        J[:, j] = (O.euler_flux(p, W + e, n) - O.euler_flux(p, W - e, n)) / 2e-6
+    lam = np.sort(np.linalg.eigvals(J).real)
+    rho = W[0]
+    U = W[1:4] / rho
+    T = (W[4] - 0.5 * rho * U @ U) / (2.5 * rho * R)
+    a = math.sqrt(1.4 * R * T)
+    Un = U @ n
+    assert np.allclose(lam, np.sort([Un - a, Un, Un, Un, Un, Un + a]), atol=1e-6)
+    # spectral radius: largest |eigenvalue| plus the viscous term
+    r = O.spectral_radius(p, W, n, 0.1)
+    Ttr = (W[4] - 0.5 * rho * U @ U - W[5]) / (1.5 * rho * R)
+    visc = 2 * p.mu_ref * Ttr ** p.omega_vis / (rho * 0.1)
+    assert abs(r - (np.abs(lam).max() + visc)) < 1e-6
+
+
+# ---------------------------------------------------------------------------------
+# P11: least squares and limiter
+# ---------------------------------------------------------------------------------
+def test_venkatakrishnan_function():
+    assert O.venkat(0.3, 0.0, 1e-3) == 1.0
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        d1, d2 = rng.random(2) * 2
+        psi = O.venkat(d1, d2, 0.0)
+        assert psi >= 0 and psi * d2 <= d1 * (1 + 1e-14)       # bounded extrapolation
+        assert abs(O.venkat(-d1, -d2, 0.1) - O.venkat(d1, d2, 0.1)) < 1e-14
+    assert O.venkat(0.0, 0.5, 0.0) == 0.0                       # local extremum: flat
+
+
+def test_least_squares_exact_for_linear_data():
+    wl = TW.tiny_tet(lim=0)
+    o = O.Oracle(wl)
+    rng = np.random.default_rng(2)
+    a = rng.random(o.K)
+    b = rng.standard_normal((o.K, 3))
+    x = wl.mesh.cell_center
+    phi = np.stack([a[None, :] + x @ b.T, 2 * a[None, :] - x @ b.T])   # [2, N, K]
+    o.put(O.BUF_PHI, phi)
+    o.step("gradient")
+    g = o.get(O.BUF_GRAD)                                              # [2, 3, N, K]
+    interior = np.ones(o.N, bool)
+    fc = wl.mesh.face_cell
+    interior[fc[fc[:, 1] < 0, 0]] = False
+    assert interior.sum() > 10
+    assert np.abs(g[0][:, interior] - b.T[:, None, :]).max() < 1e-11
+    assert np.abs(g[1][:, interior] + b.T[:, None, :]).max() < 1e-11
+
+
+def test_limited_reconstruction_within_neighbour_bounds():
+    wl = TW.tiny_tet(lim=1)
+    wl.params.lim_k = 1e-9                      # eps^2 -> 0
+    o = O.Oracle(wl)
+    rng = np.random.default_rng(5)
+    phi = rng.random((2, o.N, o.K))
+    o.put(O.BUF_PHI, phi)
+    o.step("gradient")
+    g = o.get(O.BUF_GRAD)
+    m = wl.mesh
+    nb = [[] for _ in range(o.N)]
+    fof = [[] for _ in range(o.N)]
+    for f, (a, b) in enumerate(m.face_cell):
+        fof[a].append(f)
+        if b >= 0:
+            nb[a].append(b); nb[b].append(a); fof[b].append(f)
+    for i in range(o.N):
+        lo = np.minimum(phi[:, i], phi[:, nb[i]].min(axis=1))
+        hi = np.maximum(phi[:, i], phi[:, nb[i]].max(axis=1))
+        for f in fof[i]:
+            r = m.face_center[f] - m.cell_center[i]
+            val = phi[:, i] + np.einsum("d,fdk->fk", r, g[:, :, i])
+            assert np.all(val >= lo - 1e-12) and np.all(val <= hi + 1e-12)
+
+
+# ---------------------------------------------------------------------------------
+# P10: telescoping of face fluxes; zero mass flux through diffuse walls
+# ---------------------------------------------------------------------------------
+def test_flux_telescoping_and_wall_mass_flux():
+    wl = TW.tiny_tet()
+    o = O.Oracle(wl)
+    o.iterate(2)
+    for st in ("gradient", "faces", "fluxes"):
+        o.step(st)
+    m = wl.mesh
+    face = o.get(O.BUF_FACE)
+    u, w = wl.dvs.u, wl.dvs.w
+    V = m.cell_volume
+    bnd = np.where(m.face_cell[:, 1] < 0)[0]
+    # micro: sum_i V_i F_{i,k} = sum over boundary faces of A (u.n) phi_f
+    microF = o.get(O.BUF_MICRO_F)
+    lhs = np.einsum("i,fik->fk", V, microF)
+    rhs = np.zeros_like(lhs)
+    for f in bnd:
+        rhs += m.face_area[f] * (u @ m.face_normal[f])[None, :] * face[:, f]
+    assert _rel(lhs, rhs) < 1e-12
+    # macro
+    macroF = o.get(O.BUF_MACRO_F)
+    tot = (V[:, None] * macroF).sum(0)
+    ref = np.zeros(6)
+    for f in bnd:
+        un = u @ m.face_normal[f]
+        g, h = face[:, f]
+        ref += m.face_area[f] * np.array([w @ (un * g), *((w * un * g) @ u),
+                                          w @ (un * (0.5 * (u * u).sum(1) * g + h)), w @ (un * h)])
+    assert _rel(tot, ref) < 1e-11
+    # diffuse walls: zero discrete mass flux
+    for f in bnd[m.face_cell[bnd, 1] == -1]:
+        un = u @ m.face_normal[f]
+        flux = w @ (un * face[0, f])
+        assert abs(flux) < 1e-13 * (w @ (np.abs(un) * face[0, f]))
+
+
+def test_step6_reproduces_prediction_when_phi_equals_equilibrium():
+    """Eqs. solve_rho - solve_qrot: if phi^{n+1} equals the predicted equilibrium,
+    W^{n+1} = W~ and q^{n+1} is q~ times the printed coefficients."""
+    wl = TW.tiny_tet()
+    o = O.Oracle(wl)
+    o.iterate(2)
+    for st in ("gradient", "faces", "fluxes", "macro", "micro"):
+        o.step(st)
+    Wt = o.get(O.BUF_WT)
+    q = o.get(O.BUF_Q)
+    phi = o.get(O.BUF_PHI)
+    eq = np.zeros_like(phi)
+    Z = wl.params.Z_rot
+    for i in range(o.N):
+        rho = Wt[i, 0]
+        U = Wt[i, 1:4] / rho
+        ke = 0.5 * rho * U @ U
+        T = (Wt[i, 4] - ke) / (2.5 * rho * R)
+        Ttr = (Wt[i, 4] - ke - Wt[i, 5]) / (1.5 * rho * R)
+        Trot = Wt[i, 5] / (rho * R)
+        s = O.make_state(rho, U, T, Ttr, Trot, q[i, :3], q[i, 3:])
+        eq[:, i] = O.equilibrium(wl.params, s, wl.dvs.u)
+    o.put(O.BUF_DPHI, eq - phi)
+    o.step("update")
+    W1 = o.get(O.BUF_W)
+    q1 = o.get(O.BUF_Q)
+    rho = Wt[:, 0]
+    T = (Wt[:, 4] - 0.5 * (Wt[:, 1:4] ** 2).sum(1) / rho) / (2.5 * rho * R)
+    Wexp = Wt.copy()
+    Wexp[:, 5] = (1 - 1 / Z) * Wt[:, 5] + rho * R * T / Z     # exact E_rot of R~*
+    assert _rel(W1, Wexp) < 1e-13
+    atr = (1 - (1 - wl.params.omega0) / Z) / 3
+    arot = (1 - wl.params.delta) * (1 - (1 - wl.params.omega1) / Z)
+    assert np.abs(q1[:, :3] - atr * q[:, :3]).max() < 1e-13
+    assert np.abs(q1[:, 3:] - arot * q[:, 3:]).max() < 1e-13
