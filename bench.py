@@ -1,0 +1,319 @@
+"""Benchmark of the implicit Rykov iteration on GB300.
+
+One step = one full implicit iteration (Steps 2-6: reconstruction, interface
+collision and fluxes, macro PR-SGS prediction, micro PR-SGS, compensated update)
+over every (cell, velocity) pair of the sphere workload: Mach 5, Kn 0.1 on the
+diameter, ~62k seeded Delaunay tetrahedra in a 10R box, ~3,000-point unstructured
+velocity space from the paper's DVS criterion.  Metric: cell-velocity updates/s
+(N*K / time per iteration); the wall time to residual 1e-6 is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on the
+host cores on a bounded sample of the same workload.  Under torchrun every rank
+runs an independent replica (the path has no data-path collective); rank 0 prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-velocity updates/s per implicit sweep; wall time to residual 1e-6"
+UNIT = "cell-velocity updates/s"
+START_ITERS = 10          # first-order start-up iterations, untimed
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, n = [], None, set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            n += 1
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": n}
+
+
+def workload():
+    from paper_2303_10846_gb300 import inputs as I
+    return I.sphere_workload()
+
+
+def dvs_sample(wl, stride):
+    """Every stride-th velocity of the workload's DVS (weights scaled by stride):
+    the bounded CPU sample of the same workload."""
+    import copy
+    from paper_2303_10846_gb300 import inputs as I
+    w2 = copy.copy(wl)
+    w2.dvs = I.DVS(u=wl.dvs.u[::stride].copy(), w=wl.dvs.w[::stride] * stride,
+                   name=f"{wl.dvs.name}/every{stride}")
+    return w2
+
+
+def cpu_oracle_rate(wl, iters=1, stride=10):
+    """Oracle (FP64 C, OpenMP over cells/faces) on the host cores: updates/s on a
+    DVS sample of the workload, the first `iters` implicit iterations."""
+    import oracle as O
+    w2 = dvs_sample(wl, stride)
+    o = O.Oracle(w2)
+    t0 = time.perf_counter()
+    o.iterate(iters)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return (w2.mesh.n_cell * w2.dvs.K * iters / dt, cores,
+            f"{iters} oracle iteration(s) of the full mesh (N={w2.mesh.n_cell}) with every "
+            f"{stride}th velocity (K={w2.dvs.K} of {wl.dvs.K}), {dt:.1f} s")
+
+
+def run_reference(args, rank, world):
+    out = {"metric": METRIC, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+    if rank != 0:
+        return None
+    import oracle as O
+    wl = workload()
+    stride = 30
+    w2 = dvs_sample(wl, stride)
+    o = O.Oracle(w2)
+    for _ in range(args.warmup):
+        o.iterate(1)
+    t0 = time.perf_counter()
+    o.iterate(args.steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = w2.mesh.n_cell * w2.dvs.K * args.steps / dt
+    out.update(value=v, ms_per_step=1e3 * dt / args.steps,
+               config={"workload": wl.name, "N": wl.mesh.n_cell, "K": wl.dvs.K,
+                       "sample_K": w2.dvs.K, "precision": "fp64", "l2": "n/a (CPU)"},
+               cpu_baseline={"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"full mesh, every {stride}th velocity (K={w2.dvs.K}), "
+                                       f"{args.warmup} warm-up + {args.steps} timed iterations"},
+               e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+    return out
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2303_10846_gb300.rykov import Solver
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = workload()
+    N, K = wl.mesh.n_cell, wl.dvs.K
+    s = Solver(wl, args.precision)
+    stream = s.stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # start-up (first-order iterations and the CFL ramp), then warm-up
+    s.iterate(START_ITERS)
+    s.iterate(args.warmup)
+    barrier()
+    clk = Clocks(local_rank)
+    clk.start()
+    s.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    rc, done, res = s.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof, launches_total = s.profile_get()
+    s.profile(False)
+    launches = sum(c for _, c in prof.values())
+    # per-class launch counts include event-bracketed groups; count kernels exactly
+    _, after = s.profile_get()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * K / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: upload the initial
+    # state from pinned host memory, iterate with the residual read back to the
+    # host every iteration, read W and q back
+    prim = torch.from_numpy(np.ascontiguousarray(wl.prim0)).pin_memory()
+    Wh = torch.empty((N, 6), dtype=torch.float64).pin_memory()
+    qh = torch.empty((N, 6), dtype=torch.float64).pin_memory()
+    barrier()
+    t1 = time.perf_counter()
+    s.set_state_prim(prim.numpy())
+    rc2, done2, _ = s.iterate(args.steps, tol=1e-300)
+    from paper_2303_10846_gb300.rykov import _ptr
+    s._check(s.L.rk_moments(s.h, _ptr(Wh), _ptr(qh), None, 0))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * N * K * done2 / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(prim.numel() * 8 / done2),
+           "d2h_bytes_per_step": int(6 * 8 + (Wh.numel() + qh.numel()) * 8 / done2)}
+
+    out = None
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        Tsz = 4 if args.precision == "mixed" else 8
+        # dominant kernel class and its roofline (algorithmic bytes per launch, see
+        # the design doc for the per-unit figures)
+        F, Fi = wl.mesh.n_face, int((wl.mesh.face_cell[:, 1] >= 0).sum())
+        nnz = 2 * Fi + (F - Fi)
+        algo = {
+            "recon": lambda n: (2 * N * K + 2 * F * K) * Tsz,          # read phi, write phi0
+            "face_interior": lambda n: 4 * Fi * K * Tsz,                 # read phi0, write phi_ij
+            "micro_sweep_mid": lambda n: 6 * (N * K) * Tsz / n,          # Res, dphi_j, dphi (per colour launch: N/C cells)
+            "micro_sweep_first": lambda n: (2 * N * K + 2 * nnz * K + 6 * N * K) * Tsz / n,
+            "micro_sweep_last": lambda n: 12 * (N * K) * Tsz / n,
+        }
+        top = max(prof.items(), key=lambda kv: kv[1][0])
+        name, (tms, cnt) = top
+        per_launch_ms = tms / max(cnt, 1)
+        roof = None
+        if name in algo and cnt:
+            # launches per step of that class
+            per_step = cnt / args.steps
+            bytes_launch = algo[name](per_step) if name.startswith("micro") else algo[name](1)
+            ach = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                    "peak_kind": peak_kind, "share_of_step": round(tms / (ms * args.steps), 4)}
+        # whole iteration against the 52-word per (cell, velocity) model
+        iter_bytes = 52 * Tsz * N * K
+        cpu_v, cores, sample = cpu_oracle_rate(wl) if not args.no_cpu else (None, 0, "skipped")
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "N": N, "K": K, "faces": F,
+                       "precision": args.precision,
+                       "l2": f"inputs larger than L2 (distributions {2 * N * K * Tsz / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e,
+            "gpu_launches": int(after if False else launches_total_in_region(prof)),
+            "clocks": clocks,
+            "roofline": roof,
+            "iteration_roofline": {"model_bytes_per_cell_velocity": 52 * Tsz,
+                                   "achieved": round(iter_bytes / (ms * 1e-3) / 1e9, 1),
+                                   "peak": peak, "frac": round(iter_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
+            "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "residual_after": float(np.max(res)),
+            "wall_s_timed": wall,
+        }
+    s.close()
+    return out
+
+
+def launches_total_in_region(prof):
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        out = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

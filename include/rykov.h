@@ -1,0 +1,190 @@
+/*
+ * librykov -- GB300 (sm_103a) implementation of the per-iteration hot path of the
+ * conservative implicit scheme for steady diatomic-gas flows of Zhang, Liu, Chen,
+ * Zhong and Zhuo (Rykov model, unstructured physical mesh, unstructured discrete
+ * velocity space).  One call of rk_implicit_iterate performs Steps 2-7 of the
+ * paper's Sec. 3.5 for every (cell, discrete velocity) pair on the device.
+ *
+ * Conventions for every entry point
+ *   - Return value: RK_OK (0) or a negative RK_E* code; rk_last_error() gives a
+ *     message.  No C++ exception crosses this boundary.
+ *   - All device work is enqueued on the CUDA stream given to rk_create (the
+ *     caller's stream).  Calls that return data to host memory synchronise that
+ *     stream before returning.
+ *   - The library never allocates device memory: the caller allocates one
+ *     workspace of rk_workspace_size() bytes and binds it; the library carves all
+ *     device arrays from it and never frees it.  Host pointers passed in are only
+ *     read during the call (their contents are copied); the caller keeps ownership.
+ *   - A context is not thread safe; use one context per stream.
+ *
+ * Array layouts (row-major, C order):
+ *   face_cell[F][2]   (left cell, right cell); right < 0 marks a boundary face whose
+ *                     boundary-condition id is -1-right.
+ *   face_normal[F][3] unit normal from left to right (outward at boundary faces).
+ *   W[N][6]           (rho, rho U_x, rho U_y, rho U_z, rho E, rho E_rot), Eq.
+ *                     phi_solve_mac; prim[N][6] = (rho, U_x, U_y, U_z, T_tr, T_rot).
+ *   q[N][6]           (q_tr x,y,z, q_rot x,y,z), Eqs. phi_solve_qtra / qrot.
+ *   distribution      [2][N][K_pad] in the context precision (double for RK_FP64,
+ *                     float for RK_MIXED); field 0 = G (called g), 1 = R (called h);
+ *                     K_pad = K rounded up to a multiple of 32 (rk_dims).
+ * All quantities are dimensionless as in the paper's Sec. 4 (U_ref = sqrt(2 R T_ref)).
+ */
+#ifndef RYKOV_H
+#define RYKOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RK_VERSION 100
+
+enum {
+    RK_OK = 0,
+    RK_EINVAL = -1,     /* bad argument or inconsistent input                    */
+    RK_ENOMEM = -2,     /* workspace missing or too small                        */
+    RK_ECUDA = -3,      /* a CUDA runtime call failed                            */
+    RK_EDEVICE = -4,    /* a kernel raised its device status flag                */
+    RK_EDIVERGED = -5,  /* non-finite residual                                   */
+    RK_ETIMEOUT = -6,   /* reserved: bounded device wait gave up                 */
+    RK_ESTATE = -7      /* call out of order (e.g. iterate before set_state)     */
+};
+
+enum { RK_FP64 = 0, RK_MIXED = 1 };         /* context precision                 */
+enum { RK_WALL = 0, RK_FARFIELD = 1 };      /* boundary-condition kinds          */
+
+/* Scheme parameters.  Field order and meaning are part of the ABI. */
+typedef struct rk_params {
+    double R;           /* specific gas constant (1/2 in the paper's units)       */
+    double Z_rot;       /* rotational collision number, Eq. model_equ_f           */
+    double omega_vis;   /* VHS index, Eq. T_solve_mu                              */
+    double mu_ref;      /* viscosity at T_ref                                     */
+    double T_ref;
+    double omega0, omega1, delta;   /* Rykov constants, Eqs. eqdf_Grot - Rrot     */
+    double cfl_s;       /* CFL number of Delta t_i that sets s_ij (Sec. 3.3)      */
+    double cfl_imp;     /* implicit step = cfl * Delta t_i: the largest cfl       */
+    double cfl_imp0;    /* cfl of the first iteration after set_state (<=0: none) */
+    double cfl_ramp;    /* geometric growth of cfl per iteration                  */
+    double lim_k;       /* Venkatakrishnan constant K, eps^2 = (K V^{1/3})^3      */
+    int32_t n_micro_sgs;   /* PR-SGS iterations of Eq. implicit_mic_final_equ (2) */
+    int32_t n_macro_sgs;   /* PR-SGS iterations of Eq. implicit_mac_equ_fin (40)  */
+    int32_t limiter;       /* 0 unlimited, 1 Venkatakrishnan, 2 first order       */
+    int32_t first_order_iters; /* first-order iterations after set_state          */
+} rk_params;
+
+typedef struct rk_ctx rk_ctx;
+
+int rk_version(void);
+
+/* Create a context of the given precision whose work goes to `cuda_stream`
+ * (a cudaStream_t cast to uintptr_t; 0 = legacy default stream). */
+int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream);
+int rk_destroy(rk_ctx* ctx);
+const char* rk_last_error(const rk_ctx* ctx);
+
+/* Mesh (Sec. 3.1: cells V_i, faces A_ij, n_ij, neighbour sets N(i)).  Host
+ * pointers.  cell_colour must be a proper colouring of the face-neighbour graph
+ * (it fixes the Gauss-Seidel order: colours ascending forward, descending
+ * backward).  Validates: indices, positive volumes and areas, geometric closure
+ * (sum_f A_f n_f = 0 per cell, relative 1e-8), colouring, at most 8 faces per cell.
+ * Invalidates any bound workspace. */
+int rk_upload_mesh(rk_ctx* ctx, int64_t n_cell, int64_t n_face, const int64_t* face_cell,
+                   const double* face_normal, const double* face_area,
+                   const double* face_center, const double* cell_center,
+                   const double* cell_volume, const int32_t* cell_colour);
+
+/* Discrete velocity space: points u[K][3] (DVS-cell centroids) and weights w[K]
+ * (DVS-cell volumes), Sec. 3.2 text after Eq. implicit_mac_equ_mac_flux.  Host
+ * pointers.  Invalidates any bound workspace. */
+int rk_upload_dvs(rk_ctx* ctx, int64_t K, const double* u, const double* w);
+
+int rk_set_params(rk_ctx* ctx, const rk_params* p);
+
+/* Boundary condition for faces with bc id `bc_id` (0..63).  RK_WALL: diffuse
+ * reflection with full accommodation at wall velocity U and temperature T (rho
+ * unused).  RK_FARFIELD: incoming freestream Maxwellian (rho, U, T). */
+int rk_set_bc(rk_ctx* ctx, int32_t bc_id, int32_t kind, double rho, const double* U, double T);
+
+/* Dimensions after upload: N, F, K, K_pad, number of colours, wall faces. */
+int rk_dims(const rk_ctx* ctx, int64_t out[6]);
+
+/* Bytes of device workspace needed for the uploaded mesh/DVS and precision. */
+int rk_workspace_size(rk_ctx* ctx, size_t* bytes);
+/* Bind a caller-owned device buffer (at least rk_workspace_size bytes, 256-byte
+ * aligned) and run the set-up kernels (CFL steps, s_ij, least-squares weights). */
+int rk_bind_workspace(rk_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Step 1 of Sec. 3.5: W from primitives, q (NULL = 0), and each cell's
+ * distributions set to the Rykov equilibrium of (W, q).  Host or device
+ * (on_device != 0) pointers to doubles.  Resets the iteration counter. */
+int rk_set_state_prim(rk_ctx* ctx, const double* prim, const double* q, int on_device);
+/* Restore W, q and the distribution (context precision layout above). */
+int rk_set_state(rk_ctx* ctx, const double* W, const double* q, const void* dist, int on_device);
+int rk_get_distribution(rk_ctx* ctx, void* dist, int on_device);
+
+/* Steps 2-7 repeated n_iter times; stops early once max residual < tol (tol <= 0:
+ * fixed count).  iters_done and res_out (6 doubles: rho, rho U x,y,z, rho E,
+ * rho E_rot; may be NULL) are written on return.  Residual: sum_i |W^{n+1}-W^n|
+ * / sum_i |W^n| per component (momentum normalised by sum_i |rho U|_i).
+ * Returns RK_EDIVERGED when a residual is not finite. */
+int rk_implicit_iterate(rk_ctx* ctx, int32_t n_iter, double tol, int32_t* iters_done,
+                        double res_out[6]);
+/* Residual of the last iteration. */
+int rk_residual(rk_ctx* ctx, double res_out[6]);
+
+/* Macroscopic state: W[N][6], q[N][6], T3[N][3] = (T, T_tr, T_rot); any pointer
+ * may be NULL.  Host or device doubles. */
+int rk_moments(rk_ctx* ctx, double* W, double* q, double* T3, int on_device);
+
+/* Wall quantities of the current state, Eqs. cp, cf, ch: per wall face (in face
+ * order) 8 doubles [p_w, tau_x, tau_y, tau_z, q_w, Cp, C_tau, C_h] with freestream
+ * (rho_inf, U_inf, T_inf); force[3] = sum_f A_f sum_k w (u.n) u G_w (force of the
+ * gas on the walls) and heat = sum_f A_f q_w.  Host pointers. */
+int rk_surface(rk_ctx* ctx, double rho_inf, const double* U_inf, double T_inf,
+               double* per_wall_face, double force[3], double* heat);
+
+/* ---- step access for verification ------------------------------------------ */
+enum {
+    RK_STEP_RECON = 0,   /* LSQ gradient, limiter, reconstruction (Eq. flux_solve_phi_phi) */
+    RK_STEP_FACES = 1,   /* Step 2 (b)-(d): interface state and face distribution         */
+    RK_STEP_FLUXES = 2,  /* Step 3: macro flux per cell, spectral radii                    */
+    RK_STEP_MACRO = 3,   /* Step 4: implicit macroscopic prediction                        */
+    RK_STEP_MICRO = 4    /* Steps 5-6: micro PR-SGS, update, compensation, residual        */
+};
+/* Run one step of the iteration (in order RECON..MICRO; MICRO advances the
+ * iteration counter). */
+int rk_step(rk_ctx* ctx, int step);
+
+enum {
+    RK_BUF_PHI = 0, RK_BUF_W = 1, RK_BUF_Q = 2, RK_BUF_FACE = 4, RK_BUF_FSTATE = 6,
+    RK_BUF_MICRO_F = 7, RK_BUF_MACRO_F = 8, RK_BUF_WT = 9, RK_BUF_RES = 10,
+    RK_BUF_DPHI = 11, RK_BUF_DT = 12, RK_BUF_S = 13, RK_BUF_TAUT = 14
+};
+/* Copy an internal buffer to host memory as doubles, without K padding:
+ * PHI/MICRO_F/RES/DPHI [2][N][K], FACE [2][F][K], FSTATE [F][16], W/Q/MACRO_F/WT
+ * [N][6], DT [N][3] (CFL step, implicit step, eps^2), S [F], TAUT [N].
+ * `count` is the number of doubles the caller's buffer holds. */
+int rk_debug_get(rk_ctx* ctx, int which, double* host_out, int64_t count);
+
+/* ---- per-kernel timing ----------------------------------------------------------
+ * rk_profile(ctx, 1) makes the library bracket each kernel class below with CUDA
+ * events on its stream (an event pair per launch); rk_profile_get returns, per
+ * class, the summed device milliseconds and the launch count since the last
+ * rk_profile call, plus in counts[RK_PROF_N] the total number of kernels launched
+ * by this context since creation (with or without profiling).  Reading the
+ * events synchronises the stream. */
+enum {
+    RK_PROF_RECON = 0, RK_PROF_FACE_INT = 1, RK_PROF_FACE_BND = 2, RK_PROF_FLUXES = 3,
+    RK_PROF_MACRO = 4, RK_PROF_MICRO_FIRST = 5, RK_PROF_MICRO_MID = 6,
+    RK_PROF_MICRO_LAST = 7, RK_PROF_UPDATE = 8, RK_PROF_N = 9
+};
+int rk_profile(rk_ctx* ctx, int enable);
+/* ms[RK_PROF_N], counts[RK_PROF_N + 1] */
+int rk_profile_get(rk_ctx* ctx, double* ms, int64_t* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

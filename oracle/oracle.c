@@ -916,6 +916,7 @@ void orc_step_update(orc_ctx* c, double res_out[6]) {
     }
     for (int m = 0; m < 6; ++m) res_out[m] = num[m] / (den[m] > 1e-300 ? den[m] : 1e-300);
     free(Wold);
+    c->iter++;
 }
 
 int orc_iterate(orc_ctx* c, int32_t n_iter, double tol, int32_t* iters_done, double res_out[6]) {
@@ -929,7 +930,6 @@ int orc_iterate(orc_ctx* c, int32_t n_iter, double tol, int32_t* iters_done, dou
         orc_step_macro(c);
         orc_step_micro(c);
         orc_step_update(c, res);
-        c->iter++;
         double mx = 0.0;
         int bad = 0;
         for (int m = 0; m < 6; ++m) {

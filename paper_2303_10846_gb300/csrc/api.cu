@@ -1,0 +1,725 @@
+// Host side of librykov: the C ABI declared in include/rykov.h.  Validates and
+// stages the mesh and velocity space, builds the cell->face incidence lists and the
+// colour schedule, carves every device array out of the caller's workspace, and
+// enqueues the kernel sequence of one implicit iteration on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rykov.h"
+#include "rykov_launch.cuh"
+
+namespace {
+
+constexpr int MAX_BC = 64;
+constexpr int RK_DEBUG_FLAG = 0x100;   // precision flag: reserve verification buffers
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename X>
+    X* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        X* p = base ? reinterpret_cast<X*>(base + off) : nullptr;
+        off += n * sizeof(X);
+        return p;
+    }
+};
+
+}  // namespace
+
+struct rk_ctx {
+    int prec = RK_FP64;
+    bool debug = false;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    rk_params p{};
+    bool have_params = false;
+    // staged inputs
+    int64_t N = 0, F = 0, K = 0;
+    std::vector<int64_t> fc;
+    std::vector<double> fn, fa, fx, cx, cv;
+    std::vector<int32_t> col;
+    std::vector<double> u, w;
+    int bck[MAX_BC];
+    double bcv[MAX_BC * 5];
+    // derived (host)
+    int Kp = 0, C = 0, nnz = 0, Fi = 0, Fb = 0, nwall = 0;
+    std::vector<int> slot_off, slot_face, slot_nbr, slot_left, slot_ncol, face_int, face_bnd,
+        col_off, col_cell, wall_b, fc32;
+    std::vector<double> slot_n;
+    bool mesh_ok = false, dvs_ok = false;
+    // device
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool bound = false;
+    rk::Dev<double> dd{};
+    rk::Dev<float> df{};
+    rk::Sched sched{};
+    rk::Prof prof{};
+    double *stage_a = nullptr, *stage_b = nullptr;   // [N][6] staging for host inputs
+    double* surf_out = nullptr;                       // [nwall][8]
+    double* surf_contrib = nullptr;                   // [nwall][4]
+    double* surf_tot = nullptr;                       // [4]
+    int* wall_b_dev = nullptr;
+    void* dbg = nullptr;                              // [2][N][Kp] T (debug contexts)
+    double* pin = nullptr;                            // pinned host: 16 doubles
+    int64_t iter = 0;
+    bool have_state = false;
+    double last_res[6] = {0, 0, 0, 0, 0, 0};
+};
+
+static int fail(rk_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, RK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static double implicit_cfl(const rk_params& p, int64_t n) {
+    if (p.cfl_imp0 <= 0.0 || p.cfl_ramp <= 1.0) return p.cfl_imp;
+    double c = p.cfl_imp0 * std::pow(p.cfl_ramp, (double)n);
+    return c < p.cfl_imp ? c : p.cfl_imp;
+}
+
+extern "C" int rk_version(void) { return RK_VERSION; }
+
+extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
+    if (!out) return RK_EINVAL;
+    int base = precision & 0xff;
+    if (base != RK_FP64 && base != RK_MIXED) return RK_EINVAL;
+    rk_ctx* ctx = new (std::nothrow) rk_ctx();
+    if (!ctx) return RK_ENOMEM;
+    ctx->prec = base;
+    ctx->debug = (precision & RK_DEBUG_FLAG) != 0;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
+    std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
+    if (cudaMallocHost(&ctx->pin, 16 * sizeof(double)) != cudaSuccess) {
+        delete ctx;
+        return RK_ECUDA;
+    }
+    rk_params d{};
+    d.R = 0.5; d.Z_rot = 3.5; d.omega_vis = 0.74; d.mu_ref = 0.05; d.T_ref = 1.0;
+    d.omega0 = 0.2354; d.omega1 = 0.3049; d.delta = 1.0 / 1.55; d.cfl_s = 0.8;
+    d.cfl_imp = 1e3; d.cfl_imp0 = 0.0; d.cfl_ramp = 1.0; d.lim_k = 0.1;
+    d.n_micro_sgs = 2; d.n_macro_sgs = 40; d.limiter = 1; d.first_order_iters = 0;
+    ctx->p = d;
+    *out = ctx;
+    return RK_OK;
+}
+
+extern "C" int rk_destroy(rk_ctx* ctx) {
+    if (!ctx) return RK_EINVAL;
+    if (ctx->pin) cudaFreeHost(ctx->pin);
+    for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+    delete ctx;
+    return RK_OK;
+}
+
+extern "C" const char* rk_last_error(const rk_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
+    if (!ctx || !p) return RK_EINVAL;
+    if (!(p->R > 0) || !(p->Z_rot >= 1.0) || !(p->mu_ref > 0) || !(p->T_ref > 0) ||
+        !(p->cfl_s > 0) || !(p->cfl_imp > 0) || p->n_micro_sgs < 1 || p->n_macro_sgs < 0 ||
+        p->limiter < 0 || p->limiter > 2 || !(p->lim_k >= 0))
+        return fail(ctx, RK_EINVAL, "rk_set_params: parameter out of range");
+    bool geo_change = ctx->p.cfl_s != p->cfl_s || ctx->p.lim_k != p->lim_k;
+    ctx->p = *p;
+    ctx->have_params = true;
+    if (ctx->bound && geo_change) {
+        ctx->dd.cfl_s = ctx->df.cfl_s = p->cfl_s;
+        ctx->dd.lim_k = ctx->df.lim_k = p->lim_k;
+    }
+    auto fill = [&](auto& d) {
+        d.R = p->R; d.Z = p->Z_rot; d.omega_vis = p->omega_vis; d.mu_ref = p->mu_ref;
+        d.T_ref = p->T_ref; d.omega0 = p->omega0; d.omega1 = p->omega1; d.delta = p->delta;
+        d.cfl_s = p->cfl_s; d.lim_k = p->lim_k;
+    };
+    fill(ctx->dd);
+    fill(ctx->df);
+    if (ctx->bound && geo_change) {
+        cudaError_t e = ctx->prec == RK_FP64 ? rk::Launch<double>::setup(ctx->dd, ctx->stream)
+                                             : rk::Launch<float>::setup(ctx->df, ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return RK_OK;
+}
+
+extern "C" int rk_set_bc(rk_ctx* ctx, int32_t bc_id, int32_t kind, double rho, const double* U, double T) {
+    if (!ctx || !U) return RK_EINVAL;
+    if (bc_id < 0 || bc_id >= MAX_BC) return fail(ctx, RK_EINVAL, "rk_set_bc: bc id out of range");
+    if (kind != RK_WALL && kind != RK_FARFIELD) return fail(ctx, RK_EINVAL, "rk_set_bc: bad kind");
+    if (!(T > 0) || (kind == RK_FARFIELD && !(rho > 0)))
+        return fail(ctx, RK_EINVAL, "rk_set_bc: non-positive temperature or density");
+    ctx->bck[bc_id] = kind;
+    double* v = ctx->bcv + 5 * bc_id;
+    v[0] = rho; v[1] = U[0]; v[2] = U[1]; v[3] = U[2]; v[4] = T;
+    if (ctx->bound) {
+        double* bcv = const_cast<double*>(ctx->prec == RK_FP64 ? ctx->dd.bcv : ctx->df.bcv);
+        int* bck = const_cast<int*>(ctx->prec == RK_FP64 ? ctx->dd.bck : ctx->df.bck);
+        CK(cudaMemcpyAsync(bcv, ctx->bcv, sizeof(ctx->bcv), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(bck, ctx->bck, sizeof(ctx->bck), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return RK_OK;
+}
+
+extern "C" int rk_upload_mesh(rk_ctx* ctx, int64_t n_cell, int64_t n_face, const int64_t* face_cell,
+                              const double* face_normal, const double* face_area,
+                              const double* face_center, const double* cell_center,
+                              const double* cell_volume, const int32_t* cell_colour) {
+    if (!ctx) return RK_EINVAL;
+    if (n_cell <= 0 || n_face <= 0 || n_cell > (1LL << 30) || n_face > (1LL << 30) || !face_cell ||
+        !face_normal || !face_area || !face_center || !cell_center || !cell_volume || !cell_colour)
+        return fail(ctx, RK_EINVAL, "rk_upload_mesh: bad sizes or null pointer");
+    ctx->bound = false;
+    ctx->mesh_ok = false;
+    ctx->have_state = false;
+    const int64_t N = n_cell, F = n_face;
+    std::vector<int> nfaces(N, 0);
+    std::vector<double> clo(3 * N, 0.0), asum(N, 0.0);
+    for (int64_t f = 0; f < F; ++f) {
+        int64_t a = face_cell[2 * f], b = face_cell[2 * f + 1];
+        if (a < 0 || a >= N || b >= N || b < -MAX_BC || a == b)
+            return fail(ctx, RK_EINVAL, "rk_upload_mesh: face " + std::to_string(f) + " has a bad cell index");
+        if (!(face_area[f] > 0))
+            return fail(ctx, RK_EINVAL, "rk_upload_mesh: non-positive face area");
+        const double* n = face_normal + 3 * f;
+        if (std::fabs(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] - 1.0) > 1e-8)
+            return fail(ctx, RK_EINVAL, "rk_upload_mesh: face normal not unit");
+        nfaces[a]++;
+        for (int d = 0; d < 3; ++d) clo[3 * a + d] += face_area[f] * n[d];
+        asum[a] += face_area[f];
+        if (b >= 0) {
+            nfaces[b]++;
+            for (int d = 0; d < 3; ++d) clo[3 * b + d] -= face_area[f] * n[d];
+            asum[b] += face_area[f];
+            if (cell_colour[a] == cell_colour[b])
+                return fail(ctx, RK_EINVAL, "rk_upload_mesh: colouring not proper at face " + std::to_string(f));
+        }
+    }
+    int C = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!(cell_volume[i] > 0)) return fail(ctx, RK_EINVAL, "rk_upload_mesh: non-positive volume");
+        if (nfaces[i] < 1 || nfaces[i] > rk::MAXF)
+            return fail(ctx, RK_EINVAL, "rk_upload_mesh: cell with 0 or more than 8 faces");
+        if (cell_colour[i] < 0 || cell_colour[i] > 255) return fail(ctx, RK_EINVAL, "rk_upload_mesh: bad colour");
+        C = std::max(C, cell_colour[i] + 1);
+        double cl = std::sqrt(clo[3 * i] * clo[3 * i] + clo[3 * i + 1] * clo[3 * i + 1] + clo[3 * i + 2] * clo[3 * i + 2]);
+        if (cl > 1e-8 * asum[i])
+            return fail(ctx, RK_EINVAL, "rk_upload_mesh: cell " + std::to_string(i) + " is not closed");
+    }
+    ctx->N = N; ctx->F = F; ctx->C = C;
+    ctx->fc.assign(face_cell, face_cell + 2 * F);
+    ctx->fn.assign(face_normal, face_normal + 3 * F);
+    ctx->fa.assign(face_area, face_area + F);
+    ctx->fx.assign(face_center, face_center + 3 * F);
+    ctx->cx.assign(cell_center, cell_center + 3 * N);
+    ctx->cv.assign(cell_volume, cell_volume + N);
+    ctx->col.assign(cell_colour, cell_colour + N);
+    // cell -> face incidences in increasing face order
+    ctx->slot_off.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) ctx->slot_off[i + 1] = ctx->slot_off[i] + nfaces[i];
+    ctx->nnz = ctx->slot_off[N];
+    ctx->slot_face.assign(ctx->nnz, 0); ctx->slot_nbr.assign(ctx->nnz, 0);
+    ctx->slot_left.assign(ctx->nnz, 0); ctx->slot_ncol.assign(ctx->nnz, -1);
+    ctx->slot_n.assign(3 * (size_t)ctx->nnz, 0.0);
+    std::vector<int> fill(N, 0);
+    ctx->face_int.clear(); ctx->face_bnd.clear();
+    ctx->fc32.assign(2 * F, 0);
+    for (int64_t f = 0; f < F; ++f) {
+        int64_t a = face_cell[2 * f], b = face_cell[2 * f + 1];
+        ctx->fc32[2 * f] = (int)a; ctx->fc32[2 * f + 1] = (int)b;
+        int64_t cells[2] = {a, b};
+        for (int side = 0; side < 2; ++side) {
+            int64_t i = cells[side];
+            if (i < 0) continue;
+            int m = ctx->slot_off[i] + fill[i]++;
+            ctx->slot_face[m] = (int)f;
+            ctx->slot_left[m] = side == 0;
+            ctx->slot_nbr[m] = (int)(side == 0 ? b : a);
+            ctx->slot_ncol[m] = (side == 0 ? (b >= 0 ? cell_colour[b] : -1) : cell_colour[a]);
+            for (int d = 0; d < 3; ++d) ctx->slot_n[(size_t)d * ctx->nnz + m] = face_normal[3 * f + d];
+        }
+        if (b >= 0) ctx->face_int.push_back((int)f);
+        else ctx->face_bnd.push_back((int)f);
+    }
+    ctx->Fi = (int)ctx->face_int.size();
+    ctx->Fb = (int)ctx->face_bnd.size();
+    ctx->col_off.assign(C + 1, 0);
+    for (int64_t i = 0; i < N; ++i) ctx->col_off[cell_colour[i] + 1]++;
+    for (int c = 0; c < C; ++c) ctx->col_off[c + 1] += ctx->col_off[c];
+    ctx->col_cell.assign(N, 0);
+    std::vector<int> cf(C, 0);
+    for (int64_t i = 0; i < N; ++i) ctx->col_cell[ctx->col_off[cell_colour[i]] + cf[cell_colour[i]]++] = (int)i;
+    ctx->mesh_ok = true;
+    return RK_OK;
+}
+
+extern "C" int rk_upload_dvs(rk_ctx* ctx, int64_t K, const double* u, const double* w) {
+    if (!ctx) return RK_EINVAL;
+    if (K <= 0 || K > (1 << 20) || !u || !w) return fail(ctx, RK_EINVAL, "rk_upload_dvs: bad size or null pointer");
+    for (int64_t k = 0; k < K; ++k)
+        if (!(w[k] > 0) || !std::isfinite(u[3 * k]) || !std::isfinite(u[3 * k + 1]) || !std::isfinite(u[3 * k + 2]))
+            return fail(ctx, RK_EINVAL, "rk_upload_dvs: non-positive weight or non-finite velocity");
+    ctx->bound = false;
+    ctx->have_state = false;
+    ctx->K = K;
+    ctx->Kp = (int)((K + 31) / 32 * 32);
+    ctx->u.assign(u, u + 3 * K);
+    ctx->w.assign(w, w + K);
+    ctx->dvs_ok = true;
+    return RK_OK;
+}
+
+extern "C" int rk_dims(const rk_ctx* ctx, int64_t out[6]) {
+    if (!ctx || !out) return RK_EINVAL;
+    int nw = 0;
+    for (int f : ctx->face_bnd) {
+        int bc = -1 - (int)ctx->fc[2 * (size_t)f + 1];
+        if (ctx->bck[bc] == RK_WALL) ++nw;
+    }
+    out[0] = ctx->N; out[1] = ctx->F; out[2] = ctx->K; out[3] = ctx->Kp; out[4] = ctx->C; out[5] = nw;
+    return RK_OK;
+}
+
+// Carve every device array; with base == nullptr only count bytes.
+template <typename T>
+static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
+    Carver cv{base};
+    const size_t N = ctx->N, F = ctx->F, Kp = ctx->Kp, nnz = ctx->nnz;
+    d.N = (int)N; d.F = (int)F; d.K = (int)ctx->K; d.Kp = (int)Kp; d.C = ctx->C;
+    d.Fi = ctx->Fi; d.Fb = ctx->Fb; d.nnz = (int)nnz;
+    d.vol = cv.take<double>(N); d.cx = cv.take<double>(3 * N);
+    d.dt = cv.take<double>(N); d.eps2 = cv.take<double>(N);
+    d.colour = cv.take<int>(N); d.slot_off = cv.take<int>(N + 1);
+    d.slot_face = cv.take<int>(nnz); d.slot_nbr = cv.take<int>(nnz);
+    d.slot_left = cv.take<int>(nnz); d.slot_ncol = cv.take<int>(nnz);
+    d.slot_n = cv.take<double>(3 * nnz); d.slot_AV = cv.take<double>(nnz);
+    d.slot_d = cv.take<double>(3 * nnz); d.slot_lsq = cv.take<double>(3 * nnz);
+    d.slot_nT = cv.take<T>(3 * nnz); d.slot_AVT = cv.take<T>(nnz); d.slot_dT = cv.take<T>(3 * nnz);
+    d.slot_lsqT = cv.take<T>(3 * nnz); d.slot_sT = cv.take<T>(nnz);
+    d.fc = cv.take<int>(2 * F); d.fn = cv.take<double>(3 * F); d.fa = cv.take<double>(F);
+    d.fxc = cv.take<double>(3 * F); d.fs = cv.take<double>(F); d.fdl = cv.take<double>(F);
+    d.rf = cv.take<double>(F);
+    d.face_int = cv.take<int>(ctx->Fi + 1); d.face_bnd = cv.take<int>(ctx->Fb + 1);
+    d.bcv = cv.take<double>(MAX_BC * 5); d.bck = cv.take<int>(MAX_BC);
+    d.u = cv.take<double>(3 * Kp); d.w = cv.take<double>(Kp);
+    d.uT = cv.take<T>(3 * Kp); d.wT = cv.take<T>(Kp);
+    d.phi = cv.take<T>(2 * N * Kp); d.face = cv.take<T>(2 * F * Kp);
+    d.res = cv.take<T>(2 * N * Kp); d.dphi = cv.take<T>(2 * N * Kp);
+    d.W = cv.take<double>(6 * N); d.q = cv.take<double>(6 * N); d.Wold = cv.take<double>(6 * N);
+    d.fstate = cv.take<double>(rk::FST * F); d.mface = cv.take<double>(6 * F);
+    d.wallq = cv.take<double>(8 * (size_t)(ctx->Fb + 1));
+    d.macroF = cv.take<double>(6 * N); d.dW = cv.take<double>(6 * N); d.Wt = cv.take<double>(6 * N);
+    d.ceq = cv.take<double>(rk::EQN * N); d.taut = cv.take<double>(N); d.S = cv.take<double>(12 * N);
+    d.cellres = cv.take<double>(12 * N); d.res12 = cv.take<double>(16);
+    d.status = cv.take<int>(4);
+    int* col_cell = cv.take<int>(N);
+    ctx->sched.col_cell = col_cell;
+    ctx->stage_a = cv.take<double>(6 * N);
+    ctx->stage_b = cv.take<double>(6 * N);
+    ctx->surf_out = cv.take<double>(8 * (size_t)(ctx->Fb + 1));
+    ctx->surf_contrib = cv.take<double>(4 * (size_t)(ctx->Fb + 1));
+    ctx->surf_tot = cv.take<double>(4);
+    ctx->wall_b_dev = cv.take<int>(ctx->Fb + 1);
+    ctx->dbg = ctx->debug ? (void*)cv.take<T>(2 * N * Kp) : nullptr;
+    return cv.off + 256;
+}
+
+extern "C" int rk_workspace_size(rk_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return RK_EINVAL;
+    if (!ctx->mesh_ok || !ctx->dvs_ok) return fail(ctx, RK_ESTATE, "rk_workspace_size: upload mesh and DVS first");
+    *bytes = ctx->prec == RK_FP64 ? carve(ctx, nullptr, ctx->dd) : carve(ctx, nullptr, ctx->df);
+    return RK_OK;
+}
+
+template <typename T>
+static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
+    carve(ctx, ctx->ws, d);
+    const size_t N = ctx->N, F = ctx->F, Kp = ctx->Kp, nnz = ctx->nnz, K = ctx->K;
+    cudaStream_t s = ctx->stream;
+    auto h2d = [&](const void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    // host-side staging in device layouts (kept alive until the stream syncs)
+    std::vector<double> cxs(3 * N), fns(3 * F), fxs(3 * F);
+    for (size_t i = 0; i < N; ++i)
+        for (int r = 0; r < 3; ++r) cxs[r * N + i] = ctx->cx[3 * i + r];
+    for (size_t f = 0; f < F; ++f)
+        for (int r = 0; r < 3; ++r) { fns[r * F + f] = ctx->fn[3 * f + r]; fxs[r * F + f] = ctx->fx[3 * f + r]; }
+    std::vector<double> us(3 * Kp, 0.0), ws(Kp, 0.0);
+    std::vector<T> uTs(3 * Kp, T(0)), wTs(Kp, T(0));
+    for (size_t k = 0; k < K; ++k) {
+        for (int r = 0; r < 3; ++r) { us[r * Kp + k] = ctx->u[3 * k + r]; uTs[r * Kp + k] = (T)ctx->u[3 * k + r]; }
+        ws[k] = ctx->w[k];
+        wTs[k] = (T)ctx->w[k];
+    }
+    ctx->wall_b.clear();
+    for (int b = 0; b < ctx->Fb; ++b) {
+        int bc = -1 - ctx->fc32[2 * (size_t)ctx->face_bnd[b] + 1];
+        if (ctx->bck[bc] < 0) return fail(ctx, RK_EINVAL, "rk_bind_workspace: boundary id " + std::to_string(bc) + " has no condition");
+        if (ctx->bck[bc] == RK_WALL) ctx->wall_b.push_back(b);
+    }
+    ctx->nwall = (int)ctx->wall_b.size();
+    CK(h2d(d.vol, ctx->cv.data(), N * 8));
+    CK(h2d(d.cx, cxs.data(), 3 * N * 8));
+    CK(h2d(d.colour, ctx->col.data(), N * 4));
+    CK(h2d(d.slot_off, ctx->slot_off.data(), (N + 1) * 4));
+    CK(h2d(d.slot_face, ctx->slot_face.data(), nnz * 4));
+    CK(h2d(d.slot_nbr, ctx->slot_nbr.data(), nnz * 4));
+    CK(h2d(d.slot_left, ctx->slot_left.data(), nnz * 4));
+    CK(h2d(d.slot_ncol, ctx->slot_ncol.data(), nnz * 4));
+    CK(h2d(d.slot_n, ctx->slot_n.data(), 3 * nnz * 8));
+    CK(h2d(d.fc, ctx->fc32.data(), 2 * F * 4));
+    CK(h2d(d.fn, fns.data(), 3 * F * 8));
+    CK(h2d(d.fa, ctx->fa.data(), F * 8));
+    CK(h2d(d.fxc, fxs.data(), 3 * F * 8));
+    if (ctx->Fi) CK(h2d(d.face_int, ctx->face_int.data(), ctx->Fi * 4));
+    if (ctx->Fb) CK(h2d(d.face_bnd, ctx->face_bnd.data(), ctx->Fb * 4));
+    if (ctx->nwall) CK(h2d(ctx->wall_b_dev, ctx->wall_b.data(), ctx->nwall * 4));
+    CK(h2d(d.bcv, ctx->bcv, sizeof(ctx->bcv)));
+    CK(h2d(d.bck, ctx->bck, sizeof(ctx->bck)));
+    CK(h2d(d.u, us.data(), 3 * Kp * 8));
+    CK(h2d(d.w, ws.data(), Kp * 8));
+    CK(h2d(d.uT, uTs.data(), 3 * Kp * sizeof(T)));
+    CK(h2d(d.wT, wTs.data(), Kp * sizeof(T)));
+    CK(h2d(ctx->sched.col_cell, ctx->col_cell.data(), N * 4));
+    ctx->sched.col_off = ctx->col_off;
+    // zero the distribution-sized arrays once so that the K padding stays 0
+    CK(cudaMemsetAsync(d.phi, 0, 2 * N * Kp * sizeof(T), s));
+    CK(cudaMemsetAsync(d.face, 0, 2 * F * Kp * sizeof(T), s));
+    CK(cudaMemsetAsync(d.res, 0, 2 * N * Kp * sizeof(T), s));
+    CK(cudaMemsetAsync(d.dphi, 0, 2 * N * Kp * sizeof(T), s));
+    CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(int), s));
+    CK(cudaMemsetAsync(d.wallq, 0, 8 * (size_t)(ctx->Fb + 1) * 8, s));
+    CK(cudaMemsetAsync(d.fstate, 0, rk::FST * F * 8, s));
+    cudaError_t e = rk::Launch<T>::setup(d, s);
+    if (e != cudaSuccess) return fail(ctx, RK_ECUDA, std::string("setup kernels: ") + cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(s));
+    ctx->bound = true;
+    ctx->have_state = false;
+    return RK_OK;
+}
+
+extern "C" int rk_bind_workspace(rk_ctx* ctx, void* dev_ptr, size_t bytes) {
+    if (!ctx || !dev_ptr) return RK_EINVAL;
+    if (!ctx->mesh_ok || !ctx->dvs_ok) return fail(ctx, RK_ESTATE, "rk_bind_workspace: upload mesh and DVS first");
+    size_t need = 0;
+    rk_workspace_size(ctx, &need);
+    if (bytes < need) return fail(ctx, RK_ENOMEM, "rk_bind_workspace: workspace too small (" + std::to_string(bytes) + " < " + std::to_string(need) + ")");
+    if (reinterpret_cast<uintptr_t>(dev_ptr) & 255) return fail(ctx, RK_EINVAL, "rk_bind_workspace: pointer not 256-byte aligned");
+    ctx->ws = static_cast<char*>(dev_ptr);
+    ctx->ws_bytes = bytes;
+    rk_set_params(ctx, &ctx->p);
+    return ctx->prec == RK_FP64 ? bind_impl(ctx, ctx->dd) : bind_impl(ctx, ctx->df);
+}
+
+static int need_bound(rk_ctx* ctx, const char* who) {
+    if (!ctx) return RK_EINVAL;
+    if (!ctx->bound) return fail(ctx, RK_ESTATE, std::string(who) + ": bind a workspace first");
+    return RK_OK;
+}
+
+template <typename T>
+static int set_state_prim_impl(rk_ctx* ctx, rk::Dev<T>& d, const double* prim, const double* q, int on_device) {
+    const size_t N = ctx->N;
+    const double* pd = prim;
+    const double* qd = q;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(ctx->stage_a, prim, 6 * N * 8, cudaMemcpyHostToDevice, ctx->stream));
+        pd = ctx->stage_a;
+        if (q) {
+            CK(cudaMemcpyAsync(ctx->stage_b, q, 6 * N * 8, cudaMemcpyHostToDevice, ctx->stream));
+            qd = ctx->stage_b;
+        }
+    }
+    cudaError_t e = rk::Launch<T>::set_state(d, ctx->stream, pd, qd);
+    if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->iter = 0;
+    ctx->have_state = true;
+    return RK_OK;
+}
+
+extern "C" int rk_set_state_prim(rk_ctx* ctx, const double* prim, const double* q, int on_device) {
+    int rc = need_bound(ctx, "rk_set_state_prim");
+    if (rc) return rc;
+    if (!prim) return fail(ctx, RK_EINVAL, "rk_set_state_prim: null prim");
+    if (!on_device) {
+        for (int64_t i = 0; i < ctx->N; ++i)
+            if (!(prim[6 * i] > 0) || !(prim[6 * i + 4] > 0) || !(prim[6 * i + 5] > 0))
+                return fail(ctx, RK_EINVAL, "rk_set_state_prim: non-positive density or temperature");
+    }
+    return ctx->prec == RK_FP64 ? set_state_prim_impl(ctx, ctx->dd, prim, q, on_device)
+                                : set_state_prim_impl(ctx, ctx->df, prim, q, on_device);
+}
+
+extern "C" int rk_set_state(rk_ctx* ctx, const double* W, const double* q, const void* dist, int on_device) {
+    int rc = need_bound(ctx, "rk_set_state");
+    if (rc) return rc;
+    if (!W || !dist) return fail(ctx, RK_EINVAL, "rk_set_state: null pointer");
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t N = ctx->N, Kp = ctx->Kp;
+    double* dW = ctx->prec == RK_FP64 ? ctx->dd.W : ctx->df.W;
+    double* dq = ctx->prec == RK_FP64 ? ctx->dd.q : ctx->df.q;
+    void* dphi = ctx->prec == RK_FP64 ? (void*)ctx->dd.phi : (void*)ctx->df.phi;
+    size_t tsz = ctx->prec == RK_FP64 ? 8 : 4;
+    CK(cudaMemcpyAsync(dW, W, 6 * N * 8, kind, ctx->stream));
+    if (q) CK(cudaMemcpyAsync(dq, q, 6 * N * 8, kind, ctx->stream));
+    else CK(cudaMemsetAsync(dq, 0, 6 * N * 8, ctx->stream));
+    CK(cudaMemcpyAsync(dphi, dist, 2 * N * Kp * tsz, kind, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->iter = 0;
+    ctx->have_state = true;
+    return RK_OK;
+}
+
+extern "C" int rk_get_distribution(rk_ctx* ctx, void* dist, int on_device) {
+    int rc = need_bound(ctx, "rk_get_distribution");
+    if (rc) return rc;
+    const size_t N = ctx->N, Kp = ctx->Kp;
+    const void* src = ctx->prec == RK_FP64 ? (const void*)ctx->dd.phi : (const void*)ctx->df.phi;
+    size_t tsz = ctx->prec == RK_FP64 ? 8 : 4;
+    CK(cudaMemcpyAsync(dist, src, 2 * N * Kp * tsz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RK_OK;
+}
+
+// one step of the iteration (see RK_STEP_*)
+template <typename T>
+static int step_impl(rk_ctx* ctx, rk::Dev<T>& d, int step) {
+    cudaError_t e = cudaSuccess;
+    const int limiter = ctx->iter < ctx->p.first_order_iters ? 2 : ctx->p.limiter;
+    const double cfl = implicit_cfl(ctx->p, ctx->iter);
+    switch (step) {
+        case RK_STEP_RECON: e = rk::Launch<T>::recon(d, ctx->stream, limiter, ctx->prof); break;
+        case RK_STEP_FACES: e = rk::Launch<T>::faces(d, ctx->stream, ctx->prof); break;
+        case RK_STEP_FLUXES: e = rk::Launch<T>::fluxes(d, ctx->stream, ctx->prof); break;
+        case RK_STEP_MACRO:
+            e = rk::Launch<T>::macro(d, ctx->stream, ctx->sched, ctx->p.n_macro_sgs, cfl, ctx->prof);
+            break;
+        case RK_STEP_MICRO:
+            e = rk::Launch<T>::micro(d, ctx->stream, ctx->sched, ctx->p.n_micro_sgs, cfl, ctx->prof);
+            ctx->iter++;
+            break;
+        default: return fail(ctx, RK_EINVAL, "rk_step: unknown step");
+    }
+    if (e != cudaSuccess) return fail(ctx, RK_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return RK_OK;
+}
+
+template <typename T>
+static int read_residual(rk_ctx* ctx, rk::Dev<T>& d) {
+    CK(cudaMemcpyAsync(ctx->pin, d.res12, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pin + 8, d.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int m = 0; m < 6; ++m) ctx->last_res[m] = ctx->pin[m];
+    return RK_OK;
+}
+
+template <typename T>
+static int iterate_impl(rk_ctx* ctx, rk::Dev<T>& d, int32_t n_iter, double tol, int32_t* done, double* res_out) {
+    int32_t it = 0;
+    int rc = RK_OK;
+    for (; it < n_iter; ++it) {
+        for (int st = RK_STEP_RECON; st <= RK_STEP_MICRO; ++st)
+            if ((rc = step_impl(ctx, d, st))) return rc;
+        if (tol > 0.0 || it == n_iter - 1) {
+            if ((rc = read_residual(ctx, d))) return rc;
+            bool bad = false;
+            double mx = 0.0;
+            for (int m = 0; m < 6; ++m) {
+                if (!std::isfinite(ctx->last_res[m])) bad = true;
+                mx = std::max(mx, ctx->last_res[m]);
+            }
+            if (bad) {
+                if (done) *done = it + 1;
+                if (res_out) std::memcpy(res_out, ctx->last_res, sizeof(ctx->last_res));
+                return fail(ctx, RK_EDIVERGED, "rk_implicit_iterate: non-finite residual");
+            }
+            if (tol > 0.0 && mx < tol) { ++it; break; }
+        }
+    }
+    if (done) *done = it;
+    if (res_out) std::memcpy(res_out, ctx->last_res, sizeof(ctx->last_res));
+    return RK_OK;
+}
+
+extern "C" int rk_implicit_iterate(rk_ctx* ctx, int32_t n_iter, double tol, int32_t* iters_done, double res_out[6]) {
+    int rc = need_bound(ctx, "rk_implicit_iterate");
+    if (rc) return rc;
+    if (!ctx->have_state) return fail(ctx, RK_ESTATE, "rk_implicit_iterate: set a state first");
+    if (n_iter < 0) return fail(ctx, RK_EINVAL, "rk_implicit_iterate: negative count");
+    if (n_iter == 0) {
+        if (iters_done) *iters_done = 0;
+        if (res_out) std::memcpy(res_out, ctx->last_res, sizeof(ctx->last_res));
+        return RK_OK;
+    }
+    return ctx->prec == RK_FP64 ? iterate_impl(ctx, ctx->dd, n_iter, tol, iters_done, res_out)
+                                : iterate_impl(ctx, ctx->df, n_iter, tol, iters_done, res_out);
+}
+
+extern "C" int rk_step(rk_ctx* ctx, int step) {
+    int rc = need_bound(ctx, "rk_step");
+    if (rc) return rc;
+    if (!ctx->have_state) return fail(ctx, RK_ESTATE, "rk_step: set a state first");
+    rc = ctx->prec == RK_FP64 ? step_impl(ctx, ctx->dd, step) : step_impl(ctx, ctx->df, step);
+    if (rc) return rc;
+    if (step == RK_STEP_MICRO)
+        rc = ctx->prec == RK_FP64 ? read_residual(ctx, ctx->dd) : read_residual(ctx, ctx->df);
+    else
+        CK(cudaStreamSynchronize(ctx->stream));
+    return rc;
+}
+
+extern "C" int rk_residual(rk_ctx* ctx, double res_out[6]) {
+    if (!ctx || !res_out) return RK_EINVAL;
+    std::memcpy(res_out, ctx->last_res, sizeof(ctx->last_res));
+    return RK_OK;
+}
+
+extern "C" int rk_moments(rk_ctx* ctx, double* W, double* q, double* T3, int on_device) {
+    int rc = need_bound(ctx, "rk_moments");
+    if (rc) return rc;
+    const size_t N = ctx->N;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const double* dW = ctx->prec == RK_FP64 ? ctx->dd.W : ctx->df.W;
+    const double* dq = ctx->prec == RK_FP64 ? ctx->dd.q : ctx->df.q;
+    if (W) CK(cudaMemcpyAsync(W, dW, 6 * N * 8, kind, ctx->stream));
+    if (q) CK(cudaMemcpyAsync(q, dq, 6 * N * 8, kind, ctx->stream));
+    if (T3) {
+        cudaError_t e = ctx->prec == RK_FP64 ? rk::Launch<double>::temps(ctx->dd, ctx->stream, ctx->stage_a)
+                                             : rk::Launch<float>::temps(ctx->df, ctx->stream, ctx->stage_a);
+        if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+        CK(cudaMemcpyAsync(T3, ctx->stage_a, 3 * N * 8, kind, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RK_OK;
+}
+
+template <typename T>
+static int surface_impl(rk_ctx* ctx, rk::Dev<T>& d, double rho_inf, const double* U_inf, double T_inf,
+                        double* per, double force[3], double* heat) {
+    const int limiter = ctx->iter < ctx->p.first_order_iters ? 2 : ctx->p.limiter;
+    cudaError_t e = rk::Launch<T>::recon(d, ctx->stream, limiter, ctx->prof);
+    if (e == cudaSuccess) e = rk::Launch<T>::faces(d, ctx->stream, ctx->prof);
+    const double U2 = U_inf[0] * U_inf[0] + U_inf[1] * U_inf[1] + U_inf[2] * U_inf[2];
+    const double qd = 0.5 * rho_inf * U2;
+    if (e == cudaSuccess)
+        e = rk::Launch<T>::surface(d, ctx->stream, ctx->wall_b_dev, ctx->nwall, rho_inf * ctx->p.R * T_inf, qd,
+                                   std::sqrt(U2), ctx->surf_out, ctx->surf_contrib, ctx->surf_tot);
+    if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+    if (per && ctx->nwall) CK(cudaMemcpyAsync(per, ctx->surf_out, 8 * (size_t)ctx->nwall * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pin, ctx->surf_tot, 4 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (force) { force[0] = ctx->pin[0]; force[1] = ctx->pin[1]; force[2] = ctx->pin[2]; }
+    if (heat) *heat = ctx->pin[3];
+    return RK_OK;
+}
+
+extern "C" int rk_surface(rk_ctx* ctx, double rho_inf, const double* U_inf, double T_inf,
+                          double* per_wall_face, double force[3], double* heat) {
+    int rc = need_bound(ctx, "rk_surface");
+    if (rc) return rc;
+    if (!ctx->have_state) return fail(ctx, RK_ESTATE, "rk_surface: set a state first");
+    if (!U_inf || !(rho_inf > 0) || !(T_inf > 0)) return fail(ctx, RK_EINVAL, "rk_surface: bad freestream");
+    return ctx->prec == RK_FP64 ? surface_impl(ctx, ctx->dd, rho_inf, U_inf, T_inf, per_wall_face, force, heat)
+                                : surface_impl(ctx, ctx->df, rho_inf, U_inf, T_inf, per_wall_face, force, heat);
+}
+
+// ---- verification access --------------------------------------------------------
+template <typename T>
+static int copy_dist(rk_ctx* ctx, const T* src, size_t rows, double* out) {
+    const size_t Kp = ctx->Kp, K = ctx->K;
+    std::vector<T> tmp(rows * Kp);
+    CK(cudaMemcpyAsync(tmp.data(), src, rows * Kp * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t r = 0; r < rows; ++r)
+        for (size_t k = 0; k < K; ++k) out[r * K + k] = (double)tmp[r * Kp + k];
+    return RK_OK;
+}
+
+template <typename T>
+static int debug_impl(rk_ctx* ctx, rk::Dev<T>& d, int which, double* out, int64_t count) {
+    const size_t N = ctx->N, F = ctx->F, K = ctx->K;
+    auto need = [&](size_t n) { return (int64_t)n <= count; };
+    auto d2h = [&](const double* src, size_t n) -> int {
+        if (!need(n)) return fail(ctx, RK_EINVAL, "rk_debug_get: output too small");
+        CK(cudaMemcpyAsync(out, src, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return RK_OK;
+    };
+    switch (which) {
+        case RK_BUF_PHI: return need(2 * N * K) ? copy_dist(ctx, d.phi, 2 * N, out) : RK_EINVAL;
+        case RK_BUF_RES: return need(2 * N * K) ? copy_dist(ctx, d.res, 2 * N, out) : RK_EINVAL;
+        case RK_BUF_DPHI: return need(2 * N * K) ? copy_dist(ctx, d.dphi, 2 * N, out) : RK_EINVAL;
+        case RK_BUF_FACE: return need(2 * F * K) ? copy_dist(ctx, d.face, 2 * F, out) : RK_EINVAL;
+        case RK_BUF_MICRO_F: {
+            if (!ctx->dbg) return fail(ctx, RK_ESTATE, "rk_debug_get: context not created with the debug flag");
+            if (!need(2 * N * K)) return RK_EINVAL;
+            cudaError_t e = rk::Launch<T>::debug_micro_flux(d, ctx->stream, (T*)ctx->dbg);
+            if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+            return copy_dist(ctx, (const T*)ctx->dbg, 2 * N, out);
+        }
+        case RK_BUF_W: return d2h(d.W, 6 * N);
+        case RK_BUF_Q: return d2h(d.q, 6 * N);
+        case RK_BUF_MACRO_F: return d2h(d.macroF, 6 * N);
+        case RK_BUF_WT: return d2h(d.Wt, 6 * N);
+        case RK_BUF_FSTATE: return d2h(d.fstate, rk::FST * F);
+        case RK_BUF_S: return d2h(d.fs, F);
+        case RK_BUF_TAUT: return d2h(d.taut, N);
+        case RK_BUF_DT: {
+            if (!need(3 * N)) return RK_EINVAL;
+            std::vector<double> dt(N), e2(N);
+            CK(cudaMemcpyAsync(dt.data(), d.dt, N * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(e2.data(), d.eps2, N * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            const double cfl = implicit_cfl(ctx->p, ctx->iter);
+            for (size_t i = 0; i < N; ++i) { out[3 * i] = dt[i]; out[3 * i + 1] = cfl * dt[i]; out[3 * i + 2] = e2[i]; }
+            return RK_OK;
+        }
+        default: return fail(ctx, RK_EINVAL, "rk_debug_get: unknown buffer");
+    }
+}
+
+extern "C" int rk_debug_get(rk_ctx* ctx, int which, double* host_out, int64_t count) {
+    int rc = need_bound(ctx, "rk_debug_get");
+    if (rc) return rc;
+    if (!host_out) return fail(ctx, RK_EINVAL, "rk_debug_get: null output");
+    return ctx->prec == RK_FP64 ? debug_impl(ctx, ctx->dd, which, host_out, count)
+                                : debug_impl(ctx, ctx->df, which, host_out, count);
+}
+
+extern "C" int rk_profile(rk_ctx* ctx, int enable) {
+    if (!ctx) return RK_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof.on = enable != 0;
+    ctx->prof.used = 0;
+    ctx->prof.cls.clear();
+    return RK_OK;
+}
+
+extern "C" int rk_profile_get(rk_ctx* ctx, double* ms, int64_t* counts) {
+    if (!ctx || !ms || !counts) return RK_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < RK_PROF_N; ++c) { ms[c] = 0.0; counts[c] = 0; }
+    for (size_t p = 0; p < ctx->prof.cls.size(); ++p) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ctx->prof.ev[2 * p], ctx->prof.ev[2 * p + 1]));
+        ms[ctx->prof.cls[p]] += t;
+        counts[ctx->prof.cls[p]] += 1;
+    }
+    counts[RK_PROF_N] = ctx->prof.launches;
+    return RK_OK;
+}

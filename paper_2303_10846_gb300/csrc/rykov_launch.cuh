@@ -1,0 +1,63 @@
+// Launch sequences of librykov, one explicit instantiation per precision
+// (kern_f64.cu: double, kern_f32.cu: float).  Every function enqueues on `s` and
+// returns cudaSuccess or the first launch error.
+#pragma once
+
+#include <vector>
+
+#include "rykov_dev.cuh"
+
+namespace rk {
+
+// Launch accounting and optional per-class CUDA-event timing (rk_profile).
+struct Prof {
+    bool on = false;
+    long long launches = 0;
+    std::vector<cudaEvent_t> ev;      // pool, created on enable
+    std::vector<int> cls;             // class of each recorded pair
+    size_t used = 0;                  // events used (2 per pair)
+    void begin(int c, cudaStream_t s) {
+        if (!on) return;
+        if (used + 2 > ev.size()) {
+            size_t n = ev.size();
+            ev.resize(n ? 2 * n : 1024);
+            for (size_t i = n; i < ev.size(); ++i) cudaEventCreate(&ev[i]);
+        }
+        cudaEventRecord(ev[used], s);
+        cls.push_back(c);
+    }
+    void end(cudaStream_t s) {
+        if (!on) return;
+        cudaEventRecord(ev[used + 1], s);
+        used += 2;
+    }
+};
+
+struct Sched {
+    const int* col_cell;            // device: cells grouped by colour
+    std::vector<int> col_off;       // host: colour offsets (C+1)
+};
+
+template <typename T>
+struct Launch {
+    static cudaError_t setup(const Dev<T>& d, cudaStream_t s);
+    static cudaError_t set_state(const Dev<T>& d, cudaStream_t s, const double* prim,
+                                 const double* q);
+    static cudaError_t recon(const Dev<T>& d, cudaStream_t s, int limiter, Prof& pf);
+    static cudaError_t faces(const Dev<T>& d, cudaStream_t s, Prof& pf);
+    static cudaError_t fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf);
+    static cudaError_t macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
+                             double cfl, Prof& pf);
+    static cudaError_t micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,
+                             double cfl, Prof& pf);
+    static cudaError_t debug_micro_flux(const Dev<T>& d, cudaStream_t s, T* out);
+    static cudaError_t temps(const Dev<T>& d, cudaStream_t s, double* out);
+    static cudaError_t surface(const Dev<T>& d, cudaStream_t s, const int* wall_b, int nw,
+                               double p_inf, double qdyn, double Umag, double* out,
+                               double* contrib, double* tot);
+};
+
+extern template struct Launch<double>;
+extern template struct Launch<float>;
+
+}  // namespace rk

@@ -1,0 +1,141 @@
+// Definitions of the launch sequences (included by kern_f64.cu / kern_f32.cu only).
+#pragma once
+
+#include "rykov_launch.cuh"
+
+namespace rk {
+
+constexpr int FACE_BS = 256;
+constexpr int MICRO_BS = 256;
+constexpr int RECON_BS = 128;
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+template <typename T>
+cudaError_t Launch<T>::setup(const Dev<T>& d, cudaStream_t s) {
+    k_setup_dt<T><<<d.N, 128, 0, s>>>(d);
+    k_setup_lsq<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
+    k_setup_face<T><<<cdiv(d.F, 256), 256, 0, s>>>(d);
+    k_setup_slotT<T><<<cdiv(d.nnz, 256), 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::set_state(const Dev<T>& d, cudaStream_t s, const double* prim,
+                                 const double* q) {
+    k_set_state<T><<<d.N, 128, 0, s>>>(d, prim, q);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::recon(const Dev<T>& d, cudaStream_t s, int limiter, Prof& pf) {
+    dim3 grid(d.N, cdiv(d.K, RECON_BS));
+    pf.begin(0, s);
+    k_recon<T><<<grid, RECON_BS, 0, s>>>(d, limiter);
+    pf.end(s);
+    pf.launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::faces(const Dev<T>& d, cudaStream_t s, Prof& pf) {
+    if (d.Fi) {
+        pf.begin(1, s);
+        k_face_interior<T, FACE_BS><<<d.Fi, FACE_BS, 0, s>>>(d);
+        pf.end(s);
+        pf.launches += 1;
+    }
+    if (d.Fb) {
+        pf.begin(2, s);
+        k_face_boundary<T, FACE_BS><<<d.Fb, FACE_BS, 0, s>>>(d);
+        pf.end(s);
+        pf.launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf) {
+    pf.begin(3, s);
+    k_face_radius<T><<<cdiv(d.F, 256), 256, 0, s>>>(d);
+    k_cell_macro_flux<T><<<cdiv(d.N, 256), 256, 0, s>>>(d);
+    pf.end(s);
+    pf.launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
+                             double cfl, Prof& pf) {
+    pf.begin(4, s);
+    cudaMemsetAsync(d.dW, 0, sizeof(double) * 6 * (size_t)d.N, s);
+    const int C = (int)sc.col_off.size() - 1;
+    for (int it = 0; it < n_macro; ++it) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int cc = 0; cc < C; ++cc) {
+                const int col = dir == 0 ? cc : C - 1 - cc;
+                const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
+                if (!n) continue;
+                k_macro_sweep<T><<<cdiv(n, 128), 128, 0, s>>>(d, sc.col_cell + lo, n, col,
+                                                              it == 0 && dir == 0, cfl);
+                pf.launches += 1;
+            }
+        }
+    }
+    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
+    pf.end(s);
+    pf.launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,
+                             double cfl, Prof& pf) {
+    const int C = (int)sc.col_off.size() - 1;
+    const int nsw = 2 * n_micro;
+    for (int sw = 0; sw < nsw; ++sw) {
+        const int dir = sw & 1;
+        for (int cc = 0; cc < C; ++cc) {
+            const int col = dir == 0 ? cc : C - 1 - cc;
+            const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
+            if (!n) continue;
+            // the first sweep forms Res for every cell of this colour; the last
+            // sweep applies the update and the Step-6 sums
+            pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
+            k_micro_sweep<T, MICRO_BS><<<n, MICRO_BS, 0, s>>>(d, sc.col_cell + lo, col, sw == 0,
+                                                              sw == 0, sw == nsw - 1, cfl);
+            pf.end(s);
+            pf.launches += 1;
+        }
+    }
+    pf.begin(8, s);
+    k_cell_update<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
+    k_residual_reduce<T><<<1, 256, 0, s>>>(d);
+    pf.end(s);
+    pf.launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::debug_micro_flux(const Dev<T>& d, cudaStream_t s, T* out) {
+    dim3 grid(d.N, cdiv(d.K, 128));
+    k_debug_micro_flux<T><<<grid, 128, 0, s>>>(d, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::temps(const Dev<T>& d, cudaStream_t s, double* out) {
+    k_temps<T><<<cdiv(d.N, 256), 256, 0, s>>>(d, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::surface(const Dev<T>& d, cudaStream_t s, const int* wall_b, int nw,
+                               double p_inf, double qdyn, double Umag, double* out,
+                               double* contrib, double* tot) {
+    if (nw) k_surface<T><<<cdiv(nw, 128), 128, 0, s>>>(d, wall_b, nw, p_inf, qdyn, Umag, out, contrib);
+    k_sum4<<<1, 256, 0, s>>>(contrib, nw, tot);
+    return cudaGetLastError();
+}
+
+}  // namespace rk

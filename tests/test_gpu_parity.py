@@ -1,0 +1,141 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 tolerance: 1e-10 relative (normwise per buffer: max|gpu - oracle| /
+max|oracle|).  Both sides take the upwind decisions on bit-identical u.n values;
+the remaining differences are rounding order (sums over K <= 8000 terms, FMA
+contraction on the GPU), ~1e-15 per operation, which a contracting iteration
+does not amplify beyond ~1e-12 over the tested iteration counts.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_10846_gb300 import inputs as I
+from tests import workloads as TW
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _solver(wl, prec="fp64", debug=True):
+    from paper_2303_10846_gb300.rykov import Solver
+    return Solver(wl, prec, debug=debug)
+
+
+WORKLOADS = {
+    "cavity4": lambda: TW.tiny_cavity(4, 6),
+    "tet": lambda: TW.tiny_tet(lim=1, first_order_iters=1, cfl_imp=20.0),
+    "tet_k_ragged": lambda: TW.tiny_tet(n_gh=7, lim=1, cfl_imp=20.0),      # K = 343: ragged tail
+}
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_step_by_step_fp64(name):
+    wl = WORKLOADS[name]()
+    o = O.Oracle(wl)
+    s = _solver(wl)
+    assert _rel(s.debug_get("DT"), o.get(O.BUF_DT)) < 1e-13
+    assert _rel(s.debug_get("S"), o.get(O.BUF_S)) < 1e-13
+    assert _rel(s.debug_get("PHI"), o.get(O.BUF_PHI)) < 1e-14
+    from paper_2303_10846_gb300 import rykov as RK
+    for it in range(3):
+        o.step("gradient"); o.step("faces")
+        s.step(RK.STEP_RECON); s.step(RK.STEP_FACES)
+        assert _rel(s.debug_get("FACE"), o.get(O.BUF_FACE)) < TOL64, f"face it{it}"
+        assert _rel(s.debug_get("FSTATE"), o.get(O.BUF_FSTATE)) < TOL64, f"fstate it{it}"
+        o.step("fluxes"); s.step(RK.STEP_FLUXES)
+        assert _rel(s.debug_get("MACRO_F"), o.get(O.BUF_MACRO_F)) < TOL64
+        assert _rel(s.debug_get("MICRO_F"), o.get(O.BUF_MICRO_F)) < TOL64
+        o.step("macro"); s.step(RK.STEP_MACRO)
+        assert _rel(s.debug_get("WT"), o.get(O.BUF_WT)) < TOL64
+        assert _rel(s.debug_get("TAUT"), o.get(O.BUF_TAUT)) < TOL64
+        o.step("micro"); res_o = o.step("update"); s.step(RK.STEP_MICRO)
+        assert _rel(s.debug_get("RES"), o.get(O.BUF_RES)) < TOL64
+        assert _rel(s.debug_get("DPHI"), o.get(O.BUF_DPHI)) < TOL64
+        assert _rel(s.debug_get("PHI"), o.get(O.BUF_PHI)) < TOL64
+        assert _rel(s.debug_get("W"), o.get(O.BUF_W)) < TOL64
+        assert _rel(s.debug_get("Q"), o.get(O.BUF_Q)) < TOL64
+        assert _rel(s.residual(), res_o) < 1e-8
+
+
+def test_cavity_config_200_iterations_fp64():
+    """8^3 hex cavity, 8^3 Gauss-Hermite DVS, 200 implicit iterations: the
+    steady state and its wall quantities match the oracle to 1e-10."""
+    wl = I.cavity_workload()
+    o = O.Oracle(wl)
+    s = _solver(wl, debug=False)
+    rc_o, n_o, res_o = o.iterate(200)
+    rc, n, res = s.iterate(200)
+    assert rc == 0 and rc_o == 0 and n == n_o == 200
+    W, q, _ = s.moments()
+    assert _rel(W, o.get(O.BUF_W)) < TOL64
+    assert _rel(q, o.get(O.BUF_Q)) < 1e-9
+    per, force, heat = s.surface()
+    per_o, force_o, heat_o = o.surface()
+    assert _rel(per[:, :5], per_o[:, :5]) < TOL64
+    # the net force and heat on a closed box vanish: compare on the scale of the
+    # wall pressure force
+    scale = (wl.mesh.face_area[wl.mesh.face_cell[:, 1] < 0] * per_o[:, 0]).sum()
+    assert np.abs(force - force_o).max() < TOL64 * scale
+    assert abs(heat - heat_o) < TOL64 * scale
+
+
+def test_tol_stops_early_and_reports_iterations():
+    wl = TW.tiny_cavity(4, 6)
+    s = _solver(wl, debug=False)
+    rc, n, res = s.iterate(500, tol=1e-6)
+    assert rc == 0 and n < 500 and res.max() < 1e-6
+
+
+def test_set_state_round_trip_and_restart_is_deterministic():
+    wl = TW.tiny_tet(lim=1, cfl_imp=20.0)
+    a = _solver(wl, debug=False)
+    a.iterate(3)
+    W, q, _ = a.moments()
+    dist = a.get_distribution()
+    a.iterate(2)
+    Wa, _, _ = a.moments()
+    b = _solver(wl, debug=False)
+    from paper_2303_10846_gb300.rykov import _ptr
+    b._check(b.L.rk_set_state(b.h, _ptr(np.ascontiguousarray(W)), _ptr(np.ascontiguousarray(q)),
+                              _ptr(dist), 1))
+    b.iterate(2)
+    Wb, _, _ = b.moments()
+    # restart from the saved state reproduces the continuation bit for bit (the
+    # iteration counter restarts, so use a workload without a CFL ramp)
+    assert np.array_equal(Wa, Wb)
+
+
+def test_mixed_precision_tracks_fp64_cavity():
+    """Mixed mode (FP32 distributions, compensated FP64 reductions, FP64 macro
+    solve) against the FP64 oracle on the converged cavity: wall pressure, shear,
+    heat flux and force within 1e-5 relative."""
+    wl = I.cavity_workload()
+    o = O.Oracle(wl)
+    o.iterate(120)
+    s = _solver(wl, "mixed", debug=False)
+    rc, n, res = s.iterate(120)
+    assert rc == 0
+    W, _, _ = s.moments()
+    assert _rel(W, o.get(O.BUF_W)) < 1e-5
+    per, force, heat = s.surface()
+    per_o, force_o, heat_o = o.surface()
+    assert _rel(per[:, 0], per_o[:, 0]) < 1e-5            # wall pressure
+    assert _rel(per[:, 1:4], per_o[:, 1:4]) < 1e-4        # wall shear
+    assert _rel(per[:, 4], per_o[:, 4]) < 1e-4            # wall heat flux (small, ~1e-4 of p)
+    scale = (wl.mesh.face_area[wl.mesh.face_cell[:, 1] < 0] * per_o[:, 0]).sum()
+    assert np.abs(force - force_o).max() < 1e-5 * scale
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_2303_10846_gb300.rykov import RykovError, Solver
+    wl = TW.tiny_cavity(2, 4)
+    wl.mesh.cell_colour[:] = 0                     # not a proper colouring
+    with pytest.raises(RykovError):
+        Solver(wl, "fp64")
