@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 
 METRIC = "cell-velocity updates/s per implicit sweep; wall time to residual 1e-6"
 UNIT = "cell-velocity updates/s"
-START_ITERS = 10          # first-order start-up iterations, untimed
+START_ITERS = 10          # start-up iterations (first order, CFL ramp), untimed
 
 
 def _peaks():
@@ -96,6 +96,22 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": n}
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of `world` independent replicas timed by the slowest."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 def workload():
@@ -176,12 +192,13 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     # start-up (first-order iterations and the CFL ramp), then warm-up
-    s.iterate(START_ITERS)
+    s.iterate(args.start)
     s.iterate(args.warmup)
     barrier()
     clk = Clocks(local_rank)
     clk.start()
     s.profile(True)
+    _, launches0 = s.profile_get()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -193,16 +210,11 @@ def run_gpu(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    prof, launches_total = s.profile_get()
+    prof, launches1 = s.profile_get()
     s.profile(False)
-    launches = sum(c for _, c in prof.values())
-    # per-class launch counts include event-bracketed groups; count kernels exactly
-    _, after = s.profile_get()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * K / (ms * 1e-3)
+    gpu_launches = launches1 - launches0
+    ms = max_over_ranks(ms, world, dev)
+    value = job_value(N * K, world, ms)
 
     # end to end through the public API with host buffers: upload the initial
     # state from pinned host memory, iterate with the residual read back to the
@@ -218,11 +230,8 @@ def run_gpu(args, rank, world, local_rank):
     s._check(s.L.rk_moments(s.h, _ptr(Wh), _ptr(qh), None, 0))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t1
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * N * K * done2 / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": job_value(N * K * done2, world, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(prim.numel() * 8 / done2),
            "d2h_bytes_per_step": int(6 * 8 + (Wh.numel() + qh.numel()) * 8 / done2)}
 
@@ -267,7 +276,7 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": f"inputs larger than L2 (distributions {2 * N * K * Tsz / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e,
-            "gpu_launches": int(after if False else launches_total_in_region(prof)),
+            "gpu_launches": int(gpu_launches),
             "clocks": clocks,
             "roofline": roof,
             "iteration_roofline": {"model_bytes_per_cell_velocity": 52 * Tsz,
@@ -283,10 +292,6 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-def launches_total_in_region(prof):
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -295,6 +300,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--start", type=int, default=START_ITERS)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -693,13 +693,15 @@ static void macro_point_update(orc_ctx* c, int64_t i, int first_forward, int32_t
     const orc_params* P = &c->p;
     const double Z = P->Z_rot;
     double iv = 1.0 / c->cv[i];
-    /* the rotational source and its diagonal use the current iterate of cell i
-     * (reading: rho~ R T~ and tau~ are lagged to the iterate before this update) */
+    /* rotational source (Eq. implicit_mac_equ_source_term): reading for the tilde
+     * quantities, which are unknown until the prediction is done: rho~ R T~ from the
+     * current iterate of cell i just before this update, tau~ frozen at its W^n
+     * value for the whole macro solve (c->taut holds it during the sweeps) */
     double Wc[6];
     for (int m = 0; m < 6; ++m) Wc[m] = c->W[6 * i + m] + c->dW[6 * i + m];
     double rho, U[3], T, Ttr, Trot;
     prim_from_W(P, Wc, &rho, U, &T, &Ttr, &Trot);
-    double tau = relax_time(P, rho, Ttr);
+    double tau = c->taut[i];
     double D = 1.0 / c->dtimp[i];
     double off[6] = {0};
     for (int64_t m = c->cf_off[i]; m < c->cf_off[i + 1]; ++m) {
@@ -759,6 +761,12 @@ void orc_step_macro(orc_ctx* c) {
         c->rf[f] = orc_spectral_radius(P, Wm, c->fn + 3 * f, dl);
     }
     memset(c->dW, 0, sizeof(double) * 6 * (size_t)N);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double rho, U[3], T, Ttr, Trot;
+        prim_from_W(P, c->W + 6 * i, &rho, U, &T, &Ttr, &Trot);
+        c->taut[i] = relax_time(P, rho, Ttr);
+    }
     /* n_macro_sgs x (forward colour sweep, backward colour sweep) */
     for (int32_t it = 0; it < P->n_macro_sgs; ++it) {
         for (int dir = 0; dir < 2; ++dir) {

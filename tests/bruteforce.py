@@ -237,12 +237,13 @@ class BruteForce:
             mu = P.mu_ref * (Ttr / P.T_ref) ** P.omega_vis
             r[f] = abs(U @ m.face_normal[f]) + np.sqrt(1.4 * R * T) + 2 * mu / (rho * dl)
         dW = np.zeros((self.N, 6))
+        tau_n = [self.tau(_prim(w, R)[0], _prim(w, R)[3]) for w in self.W]
         seq = self.order + self.order[::-1]
         for _ in range(P.n_macro_sgs):
             for i in seq:
                 Wc = self.W[i] + dW[i]
                 rho, U, T, Ttr, Trot = _prim(Wc, R)
-                tau = self.tau(rho, Ttr)
+                tau = tau_n[i]
                 Di = 1.0 / dtimp[i]
                 lhs = np.zeros(6)
                 for f in self.faces_of[i]:
