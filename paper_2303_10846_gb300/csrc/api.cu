@@ -322,8 +322,10 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.fstate = cv.take<double>(rk::FST * F); d.mface = cv.take<double>(6 * F);
     d.wallq = cv.take<double>(8 * (size_t)(ctx->Fb + 1));
     d.macroF = cv.take<double>(6 * N); d.dW = cv.take<double>(6 * N); d.Wt = cv.take<double>(6 * N);
-    d.ceq = cv.take<double>(rk::EQN * N); d.taut = cv.take<double>(N); d.S = cv.take<double>(12 * N);
+    d.ceq = cv.take<double>(rk::CEQ * N); d.taut = cv.take<double>(N); d.S = cv.take<double>(12 * N);
     d.cellres = cv.take<double>(12 * N); d.res12 = cv.take<double>(16);
+    d.mPc = cv.take<double>(8 * N); d.mDb = cv.take<double>(4 * N);
+    d.sG0 = cv.take<double>(6 * nnz); d.sC = cv.take<double>(2 * nnz);
     d.status = cv.take<int>(4);
     int* col_cell = cv.take<int>(N);
     ctx->sched.col_cell = col_cell;

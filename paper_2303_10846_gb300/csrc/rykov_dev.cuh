@@ -16,6 +16,7 @@ namespace rk {
 
 constexpr int MAXF = 8;        // faces per cell
 constexpr int EQN = 24;        // constants of one Rykov equilibrium (see make_eq)
+constexpr int CEQ = 28;        // per-cell record: EQN constants, 1/tau~, diagonal base
 constexpr int FST = 16;        // face state record
 constexpr double PI = 3.14159265358979323846;
 
@@ -49,6 +50,10 @@ struct Dev {
     T *phi, *face, *res, *dphi;
     double *W, *q, *Wold, *fstate, *mface, *wallq, *macroF, *dW, *Wt, *ceq, *taut, *S,
         *cellres, *res12;
+    // macro PR-SGS work: flux primitives (rho, U, rho E + p, p, rho E_rot) of the
+    // current iterate per cell, diagonal base per cell, per-slot Euler flux of the
+    // neighbour's W^n and the coefficients A/(2V), A r/(2V)
+    double *mPc, *mDb, *sG0, *sC;        // mDb: [N][4] = 1/D, 1/(D + 1/(Z tau)), 1/(Z tau)
     int* status;
 };
 
@@ -64,11 +69,21 @@ __device__ __forceinline__ double dot_rn(double ax, double ay, double az, double
 __device__ __forceinline__ float dot_rn(float ax, float ay, float az, float bx, float by, float bz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(ax, bx), __fmul_rn(ay, by)), __fmul_rn(az, bz));
 }
+// u.n for the split of the micro operator into diagonal (u.n > 0) and neighbour
+// (u.n < 0) parts: exact-rounded in FP64 (same split as the oracle), contracted in FP32
+__device__ __forceinline__ double dot_split(double ax, double ay, double az, double bx, double by,
+                                            double bz) {
+    return dot_rn(ax, ay, az, bx, by, bz);
+}
+__device__ __forceinline__ float dot_split(float ax, float ay, float az, float bx, float by, float bz) {
+    return fmaf(az, bz, fmaf(ay, by, ax * bx));
+}
 __device__ __forceinline__ double ex(double x) { return exp(x); }
 __device__ __forceinline__ float ex(float x) { return expf(x); }
 
 // Accumulators for sums over the velocity space.  FP64 mode: plain FP64 sum.  Mixed
-// mode: FP32 two-sum (Knuth) compensated sum, combined in FP64.
+// mode: Kahan-compensated FP32 sum (every operation rounded as written), combined in
+// FP64: s - c carries the running sum and its lost low-order part.
 template <typename T>
 struct Acc;
 template <>
@@ -81,13 +96,99 @@ template <>
 struct Acc<float> {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float x) {
-        float t = __fadd_rn(s, x);
-        float z = __fadd_rn(t, -s);
-        c = __fadd_rn(c, __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -z)), __fadd_rn(x, -z)));
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
+
+// Values carried by the cross-lane reductions: FP64 mode reduces doubles; mixed mode
+// reduces float-float pairs (hi + lo, two-sum arithmetic, ~44 significant bits), so
+// that no FP64 instruction is spent per lane (GB300 issues FP64 at 1/64 of the FP32
+// rate).  The two-sum of (a, b) and (b, a) gives the same bits, so butterfly results
+// are identical on every lane.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+    const float hi = __fadd_rn(s, e);
+    return FF{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return ff_norm(s, e);
+}
+template <typename T>
+struct Red;
+template <>
+struct Red<double> {
+    using V = double;
+    static __device__ __forceinline__ V from(const Acc<double>& a) { return a.s; }
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+    static __device__ __forceinline__ V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ double to_d(V v) { return v; }
+};
+template <>
+struct Red<float> {
+    using V = FF;
+    static __device__ __forceinline__ V from(const Acc<float>& a) { return ff_norm(a.s, -a.c); }
+    static __device__ __forceinline__ V zero() { return FF{0.f, 0.f}; }
+    static __device__ __forceinline__ V add(V a, V b) { return ff_add(a, b); }
+    static __device__ __forceinline__ V shfl_xor(V v, int o) {
+        return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    }
+    static __device__ __forceinline__ double to_d(V v) { return (double)v.hi + (double)v.lo; }
+};
+
+template <typename T, int NV>
+__device__ __forceinline__ void warp_red(typename Red<T>::V (&v)[NV]) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] = Red<T>::add(v[j], Red<T>::shfl_xor(v[j], o));
+    }
+}
+
+// Block reduction of NV values: warp butterflies, then the warps in order on thread
+// 0; every thread receives the totals as doubles.  smem: NV * (BS/32) values + NV doubles.
+template <typename T, int NV, int BS>
+__device__ __forceinline__ void block_red(typename Red<T>::V (&v)[NV], typename Red<T>::V* sm,
+                                          double* out) {
+    using R = Red<T>;
+    constexpr int NW = BS / 32;
+    warp_red<T, NV>(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sm[j * NW + warp] = v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < NV; ++j) {
+            typename R::V t = sm[j * NW];
+            for (int q = 1; q < NW; ++q) t = R::add(t, sm[j * NW + q]);
+            out[j] = R::to_d(t);
+        }
+    }
+    __syncthreads();
+}
+
+// Butterfly sum over the 32 lanes of a warp (every lane ends with the same bits).
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+}
 
 // Deterministic block sum of NV doubles (fixed shuffle tree, then warps in order).
 // Every thread receives the totals in v.  smem must hold NV * (BS/32) doubles.
@@ -154,30 +255,29 @@ __device__ __forceinline__ Prim prim_from_W(const double* W, double R) {
 //  11 1/(15 R T_tr p_tr)  12 1/(R T_tr)  13 rho (2 pi R T)^-1.5  14 1/(2 R T)
 //  15 omega0/(15 R T p)  16 1/(R T)  17 R T_rot  18 R T  19 (1-delta)/(R T_tr p_rot)
 //  20 omega1 (1-delta)/(R T p)  21 1 - 1/Z  22 1/Z
-template <typename T>
-__device__ void make_eq(const Dev<T>& c, double rho, const double* U, double Tq, double Ttr,
-                        double Trot, const double* qtr, const double* qrot, double* e) {
-    const double R = c.R;
-    double RTtr = R * Ttr, RT = R * Tq, RTrot = R * Trot;
-    double ptr = rho * RTtr, p = rho * RT, prot = rho * RTrot;
+template <typename T, typename S>
+__device__ void make_eq(const Dev<T>& c, S rho, const S* U, S Tq, S Ttr, S Trot, const S* qtr,
+                        const S* qrot, S* e) {
+    const S R = (S)c.R;
+    const S RTtr = R * Ttr, RT = R * Tq, RTrot = R * Trot;
+    const S ptr = rho * RTtr, p = rho * RT, prot = rho * RTrot;
     for (int d = 0; d < 3; ++d) { e[d] = U[d]; e[3 + d] = qtr[d]; e[6 + d] = qrot[d]; }
-    double a = 2.0 * PI * RTtr;
+    const S a = S(2.0 * PI) * RTtr;
     e[9] = rho / (a * sqrt(a));
-    e[10] = 1.0 / (2.0 * RTtr);
-    e[11] = 1.0 / (15.0 * RTtr * ptr);
-    e[12] = 1.0 / RTtr;
-    double b = 2.0 * PI * RT;
+    e[10] = S(1) / (S(2) * RTtr);
+    e[11] = S(1) / (S(15) * RTtr * ptr);
+    e[12] = S(1) / RTtr;
+    const S b = S(2.0 * PI) * RT;
     e[13] = rho / (b * sqrt(b));
-    e[14] = 1.0 / (2.0 * RT);
-    e[15] = c.omega0 / (15.0 * RT * p);
-    e[16] = 1.0 / RT;
+    e[14] = S(1) / (S(2) * RT);
+    e[15] = (S)c.omega0 / (S(15) * RT * p);
+    e[16] = S(1) / RT;
     e[17] = RTrot;
     e[18] = RT;
-    e[19] = (1.0 - c.delta) / (RTtr * prot);
-    e[20] = c.omega1 * (1.0 - c.delta) / (RT * p);
-    e[21] = 1.0 - 1.0 / c.Z;
-    e[22] = 1.0 / c.Z;
-    e[23] = 0.0;
+    e[19] = (S(1) - (S)c.delta) / (RTtr * prot);
+    e[20] = (S)c.omega1 * (S(1) - (S)c.delta) / (RT * p);
+    e[21] = S(1) - S(1) / (S)c.Z;
+    e[22] = S(1) / (S)c.Z;
 }
 
 template <typename T>
@@ -329,6 +429,7 @@ __global__ void k_set_state(Dev<T> c, const double* prim, const double* qin) {
         for (int d = 0; d < 6; ++d) q[d] = qin ? qin[6 * (size_t)i + d] : 0.0;
         Prim p = prim_from_W(W, c.R);
         make_eq(c, p.rho, p.U, p.T, p.Ttr, p.Trot, q, q + 3, e);
+        e[EQN - 1] = 0.0;
         for (int d = 0; d < EQN; ++d) eT[d] = (T)e[d];
     }
     __syncthreads();
@@ -345,157 +446,217 @@ __global__ void k_set_state(Dev<T> c, const double* prim, const double* qin) {
 // ------------------------------------------------------------------------------------
 // Step 2 (a): least-squares gradient, Venkatakrishnan limiter and reconstruction
 // phi(x_ij - u_k s_ij) = phi_c + (x_ij - u_k s_ij - x_c) . L grad phi_c, written by
-// the upwind cell c into the face array (Eq. flux_solve_phi_phi).  One thread per
-// (cell, k); blockIdx.x = cell, blockIdx.y = block of velocities.
+// the upwind cell c into the face array (Eq. flux_solve_phi_phi).  One block per
+// cell, velocities strided over the block; the cell's face data staged in shared
+// memory.
 // ------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(128) k_recon(Dev<T> c, int limiter) {
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS, 6) k_recon(Dev<T> c, int limiter) {
+    __shared__ int s_face[MAXF], s_nbr[MAXF], s_left[MAXF];
+    __shared__ T s_lsq[3][MAXF], s_d[3][MAXF], s_n[3][MAXF], s_s[MAXF];
     const int i = blockIdx.x;
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= c.K) return;
-    const int s0 = c.slot_off[i], s1 = c.slot_off[i + 1];
-    const size_t NK = (size_t)c.N * c.Kp;
-    const T pg = c.phi[(size_t)i * c.Kp + k], ph = c.phi[NK + (size_t)i * c.Kp + k];
-    T g[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
-    T dmax[2] = {T(0), T(0)}, dmin[2] = {T(0), T(0)};
-    for (int m = s0; m < s1; ++m) {
-        const int j = c.slot_nbr[m];
-        if (j < 0) continue;
-        const T dg = c.phi[(size_t)j * c.Kp + k] - pg;
-        const T dh = c.phi[NK + (size_t)j * c.Kp + k] - ph;
-        const T lx = c.slot_lsqT[m], ly = c.slot_lsqT[c.nnz + m], lz = c.slot_lsqT[2 * c.nnz + m];
-        g[0][0] += lx * dg; g[0][1] += ly * dg; g[0][2] += lz * dg;
-        g[1][0] += lx * dh; g[1][1] += ly * dh; g[1][2] += lz * dh;
-        dmax[0] = dg > dmax[0] ? dg : dmax[0]; dmin[0] = dg < dmin[0] ? dg : dmin[0];
-        dmax[1] = dh > dmax[1] ? dh : dmax[1]; dmin[1] = dh < dmin[1] ? dh : dmin[1];
-    }
-    T L[2] = {T(1), T(1)};
-    if (limiter == 2) {
-        L[0] = L[1] = T(0);
-    } else if (limiter == 1) {
-        const T eps2 = (T)c.eps2[i];
-        for (int m = s0; m < s1; ++m) {
-            const T dx = c.slot_dT[m], dy = c.slot_dT[c.nnz + m], dz = c.slot_dT[2 * c.nnz + m];
-#pragma unroll
-            for (int fd = 0; fd < 2; ++fd) {
-                const T d2 = g[fd][0] * dx + g[fd][1] * dy + g[fd][2] * dz;
-                const T psi = venkat(d2 > T(0) ? dmax[fd] : dmin[fd], d2, eps2);
-                L[fd] = psi < L[fd] ? psi : L[fd];      // capped at 1 (reading)
-            }
+    const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
+    if (threadIdx.x < ns) {
+        const int m = s0 + threadIdx.x, q = threadIdx.x;
+        s_face[q] = c.slot_face[m];
+        s_nbr[q] = c.slot_nbr[m];
+        s_left[q] = c.slot_left[m];
+        s_s[q] = c.slot_sT[m];
+        for (int r = 0; r < 3; ++r) {
+            s_lsq[r][q] = c.slot_lsqT[r * c.nnz + m];
+            s_d[r][q] = c.slot_dT[r * c.nnz + m];
+            s_n[r][q] = c.slot_nT[r * c.nnz + m];
         }
     }
-    const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k];
-    const size_t FK = (size_t)c.F * c.Kp;
-    for (int m = s0; m < s1; ++m) {
-        const T un = dot_rn(ux, uy, uz, c.slot_nT[m], c.slot_nT[c.nnz + m], c.slot_nT[2 * c.nnz + m]);
-        const bool up = c.slot_left[m] ? (un > T(0)) : (un <= T(0));
-        if (!up) continue;
-        const T s = c.slot_sT[m];
-        const T rx = c.slot_dT[m] - ux * s, ry = c.slot_dT[c.nnz + m] - uy * s,
-                rz = c.slot_dT[2 * c.nnz + m] - uz * s;
-        const size_t o = (size_t)c.slot_face[m] * c.Kp + k;
-        c.face[o] = pg + L[0] * (g[0][0] * rx + g[0][1] * ry + g[0][2] * rz);
-        c.face[FK + o] = ph + L[1] * (g[1][0] * rx + g[1][1] * ry + g[1][2] * rz);
+    __syncthreads();
+    const T eps2 = (T)c.eps2[i];
+    const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
+    const T* phg = c.phi + (size_t)i * c.Kp;
+    const T* phh = c.phi + NK + (size_t)i * c.Kp;
+    for (int k = threadIdx.x; k < c.K; k += BS) {
+        const T pg = phg[k], ph = phh[k];
+        T g[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+        T dmax[2] = {T(0), T(0)}, dmin[2] = {T(0), T(0)};
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            const int j = s_nbr[q];
+            if (j < 0) continue;
+            const T dg = c.phi[(size_t)j * c.Kp + k] - pg;
+            const T dh = c.phi[NK + (size_t)j * c.Kp + k] - ph;
+            const T lx = s_lsq[0][q], ly = s_lsq[1][q], lz = s_lsq[2][q];
+            g[0][0] += lx * dg; g[0][1] += ly * dg; g[0][2] += lz * dg;
+            g[1][0] += lx * dh; g[1][1] += ly * dh; g[1][2] += lz * dh;
+            dmax[0] = dg > dmax[0] ? dg : dmax[0]; dmin[0] = dg < dmin[0] ? dg : dmin[0];
+            dmax[1] = dh > dmax[1] ? dh : dmax[1]; dmin[1] = dh < dmin[1] ? dh : dmin[1];
+        }
+        T L[2] = {T(1), T(1)};
+        if (limiter == 2) {
+            L[0] = L[1] = T(0);
+        } else if (limiter == 1) {
+            // min over faces of Venkatakrishnan's psi = num/den, kept as a fraction
+            // (den > 0) so that only the minimum is divided; capped at 1 (reading)
+            T bn[2] = {T(1), T(1)}, bd[2] = {T(1), T(1)};
+#pragma unroll 1
+            for (int q = 0; q < ns; ++q) {
+                const T dx = s_d[0][q], dy = s_d[1][q], dz = s_d[2][q];
+#pragma unroll
+                for (int fd = 0; fd < 2; ++fd) {
+                    const T d2 = g[fd][0] * dx + g[fd][1] * dy + g[fd][2] * dz;
+                    if (d2 == T(0)) continue;
+                    const T d1 = d2 > T(0) ? dmax[fd] : dmin[fd];
+                    const T num = d1 * d1 + eps2 + T(2) * d1 * d2;
+                    const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + eps2;
+                    if (num * bd[fd] < bn[fd] * den) { bn[fd] = num; bd[fd] = den; }
+                }
+            }
+            L[0] = bn[0] / bd[0];
+            L[1] = bn[1] / bd[1];
+        }
+        const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k];
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            const T un = dot_rn(ux, uy, uz, s_n[0][q], s_n[1][q], s_n[2][q]);
+            const bool up = s_left[q] ? (un > T(0)) : (un <= T(0));
+            if (!up) continue;
+            const T sq = s_s[q];
+            const T rx = s_d[0][q] - ux * sq, ry = s_d[1][q] - uy * sq, rz = s_d[2][q] - uz * sq;
+            const size_t o = (size_t)s_face[q] * c.Kp + k;
+            c.face[o] = pg + L[0] * (g[0][0] * rx + g[0][1] * ry + g[0][2] * rz);
+            c.face[FK + o] = ph + L[1] * (g[1][0] * rx + g[1][1] * ry + g[1][2] * rz);
+        }
     }
 }
 
 // ------------------------------------------------------------------------------------
-// Step 2 (b)-(d) at interior faces: one block per face.
-//   pass 1: rho, rho U, rho E, sum h of phi(x_ij - u s)      (Eqs. halftime_solve_rho/U/E)
-//   state : tau, rho E_rot (Eq. halftime_solve_Erot)
-//   pass 2: heat fluxes (Eqs. halftime_solve_qtra/qrot)
-//   pass 3: phi* and phi_ij = (tau phi0 + s phi*)/(tau + s) (Eq. flux_solve_phi), in
-//           place, and the DVS quadrature of the macro flux (Eq. implicit_mac_equ_mac_flux)
+// Step 2 (b)-(d) at interior faces: one warp per face.
+//   pass 1: the 17 raw moments of phi(x_ij - u s) about a reference velocity U_r
+//           (mean of the two cells' U^n): sum w g, w g c', w h, w g c'c' (6),
+//           w g |c'|^2 c', w h c'.  They give rho, rho U, rho E (Eqs.
+//           halftime_solve_rho/U/E) and, shifted to the interface velocity
+//           U = U_r + d, the heat-flux sums of Eqs. halftime_solve_qtra/qrot without
+//           cancellation at high speed.
+//   state : tau, rho E_rot (Eq. halftime_solve_Erot), q_tr, q_rot
+//   pass 2: phi* and phi_ij = (tau phi0 + s phi*)/(tau + s) in place (Eq.
+//           flux_solve_phi) and the DVS quadrature of the macro flux (Eq.
+//           implicit_mac_equ_mac_flux)
 // ------------------------------------------------------------------------------------
-template <typename T, int BS>
-__global__ void __launch_bounds__(BS) k_face_interior(Dev<T> c) {
-    __shared__ double red[6 * (BS / 32)];
-    __shared__ double st[FST];
-    __shared__ double e[EQN];
-    __shared__ T eT[EQN + 4];
-    const int f = c.face_int[blockIdx.x];
+template <typename T, int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
+    using R = Red<T>;
+    using V = typename R::V;
+    const int lane = threadIdx.x & 31;
+    const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (fi >= c.Fi) return;                      // whole warp: no block barriers below
+    const int f = c.face_int[fi];
     const size_t FK = (size_t)c.F * c.Kp;
     T* g0 = c.face + (size_t)f * c.Kp;
     T* h0 = c.face + FK + (size_t)f * c.Kp;
-    const double R = c.R, Z = c.Z;
-    const double s = c.fs[f];
-    double v[6];
-    {
-        Acc<T> a0, a1, a2, a3, a4, a5;
-        for (int k = threadIdx.x; k < c.K; k += BS) {
-            const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k], w = c.wT[k];
-            const T g = g0[k], h = h0[k];
-            const T wg = w * g;
-            a0.add(wg); a1.add(wg * ux); a2.add(wg * uy); a3.add(wg * uz);
-            a4.add(w * (T(0.5) * (ux * ux + uy * uy + uz * uz) * g + h));
-            a5.add(w * h);
-        }
-        v[0] = a0.get(); v[1] = a1.get(); v[2] = a2.get(); v[3] = a3.get(); v[4] = a4.get(); v[5] = a5.get();
+    // reference velocity U_r (any value is exact; the mean of the cells' U^n keeps
+    // the shifted moments small)
+    T Ur[3] = {T(0), T(0), T(0)};
+    if (lane == 0) {
+        const int a = c.fc[2 * f], b = c.fc[2 * f + 1];
+        const double* Wa = c.W + 6 * (size_t)a;
+        const double* Wb = c.W + 6 * (size_t)b;
+        const T ia = T(1) / (T)Wa[0], ib = T(1) / (T)Wb[0];
+        for (int d = 0; d < 3; ++d) Ur[d] = T(0.5) * ((T)Wa[1 + d] * ia + (T)Wb[1 + d] * ib);
     }
-    block_sum<6, BS>(v, red);
-    if (threadIdx.x == 0) {
-        const double rho = v[0];
-        const double U[3] = {v[1] / rho, v[2] / rho, v[3] / rho};
-        const double ke = 0.5 * rho * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-        const double Tq = (v[4] - ke) / (2.5 * rho * R);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ur[d] = __shfl_sync(0xffffffffu, Ur[d], 0);
+    V v[17];
+    {
+        Acc<T> m[17];
+        for (int k = lane; k < c.K; k += 32) {
+            const T cx = c.uT[k] - Ur[0], cy = c.uT[c.Kp + k] - Ur[1], cz = c.uT[2 * c.Kp + k] - Ur[2];
+            const T w = c.wT[k];
+            const T wg = w * g0[k], wh = w * h0[k];
+            m[0].add(wg);
+            m[1].add(wg * cx); m[2].add(wg * cy); m[3].add(wg * cz);
+            m[4].add(wh);
+            m[5].add(wg * cx * cx); m[6].add(wg * cy * cy); m[7].add(wg * cz * cz);
+            m[8].add(wg * cx * cy); m[9].add(wg * cx * cz); m[10].add(wg * cy * cz);
+            const T wgc2 = wg * (cx * cx + cy * cy + cz * cz);
+            m[11].add(wgc2 * cx); m[12].add(wgc2 * cy); m[13].add(wgc2 * cz);
+            m[14].add(wh * cx); m[15].add(wh * cy); m[16].add(wh * cz);
+        }
+#pragma unroll
+        for (int j = 0; j < 17; ++j) v[j] = R::from(m[j]);
+    }
+    warp_red<T, 17>(v);
+    // interface state on lane 0, in the per-velocity arithmetic type T (the moments
+    // themselves are carried with compensation)
+    constexpr int NB = EQN + 2;
+    T cst[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) cst[j] = T(0);
+    if (lane == 0) {
+        T x[17];
+        for (int j = 0; j < 17; ++j) x[j] = (T)R::to_d(v[j]);
+        const T Rg = (T)c.R, Z = (T)c.Z, s = (T)c.fs[f];
+        const T rho = x[0];
+        const T d[3] = {x[1] / rho, x[2] / rho, x[3] / rho};
+        const T U[3] = {Ur[0] + d[0], Ur[1] + d[1], Ur[2] + d[2]};
+        const T tr = x[5] + x[6] + x[7];
+        const T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const T etr = T(0.5) * (tr - rho * dd);            // rho E - 1/2 rho |U|^2 - sum w h
+        const T Er0 = x[4];
+        const T Tq = (etr + Er0) / (T(2.5) * rho * Rg);
         // tau from the translational temperature of the free-transport moments
         // (reading of the circular definition of the interface tau)
-        const double Ttr0 = (v[4] - ke - v[5]) / (1.5 * rho * R);
-        const double tau = relax_time(c, rho, Ttr0);
-        const double Erot = (Z * tau * v[5] + s * rho * R * Tq) / (Z * tau + s);
+        const T Ttr0 = etr / (T(1.5) * rho * Rg);
+        const T tau = (T)c.mu_ref * pow(Ttr0 / (T)c.T_ref, (T)c.omega_vis) / (rho * Rg * Ttr0);
+        const T Erot = (Z * tau * Er0 + s * rho * Rg * Tq) / (Z * tau + s);
+        const T Trot = Erot / (rho * Rg);
+        const T Ttr = (etr + Er0 - Erot) / (T(1.5) * rho * Rg);
+        // sum w c|c|^2 g and sum w c h about U = U_r + d (c = c' - d)
+        const T Sd[3] = {x[5] * d[0] + x[8] * d[1] + x[9] * d[2],
+                         x[8] * d[0] + x[6] * d[1] + x[10] * d[2],
+                         x[9] * d[0] + x[10] * d[1] + x[7] * d[2]};
+        const T dtr = tau + s - s / T(3) * (T(1) - T(1) / Z + (T)c.omega0 / Z);
+        const T drot = tau + s - s * (T(1) - (T)c.delta) * (T(1) - T(1) / Z + (T)c.omega1 / Z);
+        T qtr[3], qrot[3];
+        for (int k = 0; k < 3; ++k) {
+            const T Qtr = x[11 + k] - T(2) * Sd[k] - tr * d[k] + T(2) * rho * dd * d[k];
+            qtr[k] = tau * T(0.5) * Qtr / dtr;
+            qrot[k] = tau * (x[14 + k] - d[k] * Er0) / drot;
+        }
+        make_eq(c, rho, U, Tq, Ttr, Trot, qtr, qrot, cst + 2);
+        cst[0] = tau / (tau + s);
+        cst[1] = s / (tau + s);
+        double* st = c.fstate + (size_t)f * FST;
         st[0] = rho; st[1] = U[0]; st[2] = U[1]; st[3] = U[2];
-        st[4] = Tq; st[5] = (v[4] - ke - Erot) / (1.5 * rho * R); st[6] = Erot / (rho * R); st[7] = tau;
+        st[4] = Tq; st[5] = Ttr; st[6] = Trot; st[7] = tau;
+        for (int k = 0; k < 3; ++k) { st[8 + k] = qtr[k]; st[11 + k] = qrot[k]; }
         st[14] = s; st[15] = 0.0;
     }
-    __syncthreads();
+    T e[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) e[j] = __shfl_sync(0xffffffffu, cst[j], 0);
+    const T nx = (T)c.fn[f], ny = (T)c.fn[c.F + f], nz = (T)c.fn[2 * c.F + f];
+    const T a = e[0], b = e[1];
+    V r6[6];
     {
-        const T Ux = (T)st[1], Uy = (T)st[2], Uz = (T)st[3];
-        Acc<T> a0, a1, a2, a3, a4, a5;
-        for (int k = threadIdx.x; k < c.K; k += BS) {
-            const T cx = c.uT[k] - Ux, cy = c.uT[c.Kp + k] - Uy, cz = c.uT[2 * c.Kp + k] - Uz, w = c.wT[k];
-            const T wg = w * (cx * cx + cy * cy + cz * cz) * g0[k];
-            const T wh = w * h0[k];
-            a0.add(wg * cx); a1.add(wg * cy); a2.add(wg * cz);
-            a3.add(wh * cx); a4.add(wh * cy); a5.add(wh * cz);
-        }
-        v[0] = a0.get(); v[1] = a1.get(); v[2] = a2.get(); v[3] = a3.get(); v[4] = a4.get(); v[5] = a5.get();
-    }
-    block_sum<6, BS>(v, red);
-    if (threadIdx.x == 0) {
-        const double tau = st[7];
-        const double dtr = tau + s - s / 3.0 * (1.0 - 1.0 / Z + c.omega0 / Z);
-        const double drot = tau + s - s * (1.0 - c.delta) * (1.0 - 1.0 / Z + c.omega1 / Z);
-        for (int d = 0; d < 3; ++d) { st[8 + d] = tau * 0.5 * v[d] / dtr; st[11 + d] = tau * v[3 + d] / drot; }
-        make_eq(c, st[0], st + 1, st[4], st[5], st[6], st + 8, st + 11, e);
-        for (int d = 0; d < EQN; ++d) eT[d] = (T)e[d];
-        eT[EQN] = (T)(tau / (tau + s));
-        eT[EQN + 1] = (T)(s / (tau + s));
-        for (int d = 0; d < FST; ++d) c.fstate[(size_t)f * FST + d] = st[d];
-    }
-    __syncthreads();
-    {
-        const T a = eT[EQN], b = eT[EQN + 1];
-        const T nx = (T)c.fn[f], ny = (T)c.fn[c.F + f], nz = (T)c.fn[2 * c.F + f];
-        Acc<T> a0, a1, a2, a3, a4, a5;
-        for (int k = threadIdx.x; k < c.K; k += BS) {
+        Acc<T> m[6];
+        for (int k = lane; k < c.K; k += 32) {
             const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k], w = c.wT[k];
             T G, H;
-            eval_eq(eT, ux, uy, uz, G, H);
+            eval_eq(e + 2, ux, uy, uz, G, H);
             const T gf = a * g0[k] + b * G;
             const T hf = a * h0[k] + b * H;
             g0[k] = gf;
             h0[k] = hf;
             const T wu = w * (ux * nx + uy * ny + uz * nz);
             const T wg = wu * gf;
-            a0.add(wg); a1.add(wg * ux); a2.add(wg * uy); a3.add(wg * uz);
-            a4.add(wu * (T(0.5) * (ux * ux + uy * uy + uz * uz) * gf + hf));
-            a5.add(wu * hf);
+            m[0].add(wg); m[1].add(wg * ux); m[2].add(wg * uy); m[3].add(wg * uz);
+            m[4].add(wu * (T(0.5) * (ux * ux + uy * uy + uz * uz) * gf + hf));
+            m[5].add(wu * hf);
         }
-        v[0] = a0.get(); v[1] = a1.get(); v[2] = a2.get(); v[3] = a3.get(); v[4] = a4.get(); v[5] = a5.get();
+#pragma unroll
+        for (int j = 0; j < 6; ++j) r6[j] = R::from(m[j]);
     }
-    block_sum<6, BS>(v, red);
-    if (threadIdx.x == 0)
-        for (int d = 0; d < 6; ++d) c.mface[(size_t)f * 6 + d] = v[d];
+    warp_red<T, 6>(r6);
+    if (lane == 0)
+        for (int d = 0; d < 6; ++d) c.mface[(size_t)f * 6 + d] = R::to_d(r6[d]);
 }
 
 // Boundary faces (reading; the paper names diffuse reflection but gives no formula):
@@ -634,65 +795,116 @@ __device__ __forceinline__ void euler_flux(const double* W, double nx, double ny
     G[5] = W[5] * Un;
 }
 
-// One point update of the macro PR-SGS (Eq. implicit_mac_equ_fin) for every cell of
-// one colour.  The rotational source and its diagonal use the current iterate of
-// the cell (reading of the tilde quantities inside the source); an update whose
-// predicted state is not admissible (rho, T_tr or T_rot not positive) is skipped.
+// flux primitives (rho, U, rho E + p, p, rho E_rot) with p = rho R T = 0.4 (rho E -
+// 1/2 rho |U|^2); false if the state is not admissible (rho, T_tr or T_rot <= 0)
+__device__ __forceinline__ bool flux_prim(const double* W, double* P) {
+    const double rho = W[0], ir = 1.0 / rho;
+    const double U[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
+    const double ke = 0.5 * rho * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    const double p = 0.4 * (W[4] - ke);
+    P[0] = rho; P[1] = U[0]; P[2] = U[1]; P[3] = U[2]; P[4] = W[4] + p; P[5] = p; P[6] = W[5];
+    P[7] = 0.0;
+    return rho > 0.0 && (W[4] - ke - W[5]) > 0.0 && W[5] > 0.0;
+}
+
+// Per-iteration set-up of the macro PR-SGS: per cell 1/D_i with
+// D_i = 1/dt + sum_j A r/(2V) (and + 1/(Z tau) for rho E_rot, tau frozen at its W^n
+// value: reading of the tilde quantities in the source), 1/(Z tau); per slot the
+// neighbour's Euler flux G_ij(W_j^n) and the coefficients A/(2V), A r/(2V); the flux
+// primitives of W^n; dW~ = 0.
 template <typename T>
-__global__ void k_macro_sweep(Dev<T> c, const int* cells, int n, int colour, int first_forward,
-                              double cfl) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int i = cells[t];
+__global__ void k_macro_prep(Dev<T> c, double cfl) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
     const double iv = 1.0 / c.vol[i];
-    double Wc[6];
-    for (int m = 0; m < 6; ++m) Wc[m] = c.W[6 * (size_t)i + m] + c.dW[6 * (size_t)i + m];
-    const Prim p = prim_from_W(Wc, c.R);
-    const double tau = relax_time(c, p.rho, p.Ttr);
     double D = 1.0 / (cfl * c.dt[i]);
-    double off[6] = {0, 0, 0, 0, 0, 0};
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
         const int f = c.slot_face[m], j = c.slot_nbr[m];
         const double A = c.fa[f] * iv;
         D += 0.5 * A * c.rf[f];
-        if (j < 0) continue;
-        if (first_forward && c.slot_ncol[m] > colour) continue;
-        double sg = c.slot_left[m] ? 1.0 : -1.0;
-        const double nx = sg * c.fn[f], ny = sg * c.fn[c.F + f], nz = sg * c.fn[2 * c.F + f];
-        const double* Wj = c.W + 6 * (size_t)j;
-        const double* dWj = c.dW + 6 * (size_t)j;
-        double Wn[6], G1[6], G0[6];
-        for (int q = 0; q < 6; ++q) Wn[q] = Wj[q] + dWj[q];
-        euler_flux(Wn, nx, ny, nz, G1);
-        euler_flux(Wj, nx, ny, nz, G0);
-        for (int q = 0; q < 6; ++q) off[q] += 0.5 * A * ((G1[q] - G0[q]) - c.rf[f] * dWj[q]);
+        c.sC[2 * (size_t)m] = 0.5 * A;
+        c.sC[2 * (size_t)m + 1] = 0.5 * A * c.rf[f];
+        if (j >= 0) {
+            const double sg = c.slot_left[m] ? 1.0 : -1.0;
+            euler_flux(c.W + 6 * (size_t)j, sg * c.fn[f], sg * c.fn[c.F + f], sg * c.fn[2 * c.F + f],
+                       c.sG0 + 6 * (size_t)m);
+        }
     }
-    const double* F = c.macroF + 6 * (size_t)i;
-    double cand[6];
-    for (int q = 0; q < 5; ++q) cand[q] = (-F[q] - off[q]) / D;
-    const double Zt = c.Z * tau;
-    const double src = (p.rho * c.R * p.T - c.W[6 * (size_t)i + 5]) / Zt;
-    cand[5] = (src - F[5] - off[5]) / (D + 1.0 / Zt);
-    double Wn[6];
-    for (int q = 0; q < 6; ++q) Wn[q] = c.W[6 * (size_t)i + q] + cand[q];
-    const Prim pn = prim_from_W(Wn, c.R);
-    if (!(pn.rho > 0.0 && pn.Ttr > 0.0 && pn.Trot > 0.0)) return;
-    for (int q = 0; q < 6; ++q) c.dW[6 * (size_t)i + q] = cand[q];
+    const Prim p = prim_from_W(c.W + 6 * (size_t)i, c.R);
+    const double izt = 1.0 / (c.Z * relax_time(c, p.rho, p.Ttr));
+    c.mDb[4 * (size_t)i] = 1.0 / D;
+    c.mDb[4 * (size_t)i + 1] = 1.0 / (D + izt);
+    c.mDb[4 * (size_t)i + 2] = izt;
+    flux_prim(c.W + 6 * (size_t)i, c.mPc + 8 * (size_t)i);
+    for (int q = 0; q < 6; ++q) c.dW[6 * (size_t)i + q] = 0.0;
 }
 
-// W~ = W^n + dW~, tau~ and the constants of the predicted equilibrium phi~* built
-// from (W~, q^n) (reading: the prediction gives no heat flux, so the last Step-6
-// value is used).
+// One point update of the macro PR-SGS (Eq. implicit_mac_equ_fin) for every cell of
+// one colour, one thread per cell:
+//   dW~_i = [Res_i - sum_j (A/2V) ((G(W_j + dW~_j) - G(W_j)) - r dW~_j)] / D_i,
+// the flux Jacobian applied matrix-free with the neighbours' cached flux
+// primitives; rho~ R T~ of the rotational source from the cell's current iterate.
+// An update whose predicted state is not admissible (rho, T_tr or T_rot not
+// positive) is skipped.
 template <typename T>
-__global__ void k_macro_finish(Dev<T> c) {
+__global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* cells, int n, int colour,
+                                                     int first_forward) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i = cells[t];
+    double o[6] = {0, 0, 0, 0, 0, 0};
+    for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
+        const int j = c.slot_nbr[m];
+        if (j < 0 || (first_forward && c.slot_ncol[m] > colour)) continue;
+        const int f = c.slot_face[m];
+        const double sg = c.slot_left[m] ? 1.0 : -1.0;
+        const double nx = sg * c.fn[f], ny = sg * c.fn[c.F + f], nz = sg * c.fn[2 * c.F + f];
+        const double* P = c.mPc + 8 * (size_t)j;
+        const double Un = P[1] * nx + P[2] * ny + P[3] * nz;
+        const double rU = P[0] * Un;
+        const double G1[6] = {rU, rU * P[1] + P[5] * nx, rU * P[2] + P[5] * ny, rU * P[3] + P[5] * nz,
+                              P[4] * Un, P[6] * Un};
+        const double* G0 = c.sG0 + 6 * (size_t)m;
+        const double* dWj = c.dW + 6 * (size_t)j;
+        const double c1 = c.sC[2 * (size_t)m], c2 = c.sC[2 * (size_t)m + 1];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) o[q] += c1 * (G1[q] - G0[q]) - c2 * dWj[q];
+    }
+    const double* W = c.W + 6 * (size_t)i;
+    double* dW = c.dW + 6 * (size_t)i;
+    // rho R T of the current iterate: (2/5)(rho E - |rho U|^2 / (2 rho))
+    const double rc = W[0] + dW[0];
+    const double mx = W[1] + dW[1], my = W[2] + dW[2], mz = W[3] + dW[3];
+    const double rRT = 0.4 * (W[4] + dW[4] - 0.5 * (mx * mx + my * my + mz * mz) / rc);
+    const double* F = c.macroF + 6 * (size_t)i;
+    const double iD = c.mDb[4 * (size_t)i], iDr = c.mDb[4 * (size_t)i + 1], izt = c.mDb[4 * (size_t)i + 2];
+    double cand[6];
+    for (int q = 0; q < 5; ++q) cand[q] = (-F[q] - o[q]) * iD;
+    cand[5] = ((rRT - W[5]) * izt - F[5] - o[5]) * iDr;
+    double Wn[6], Pn[8];
+    for (int q = 0; q < 6; ++q) Wn[q] = W[q] + cand[q];
+    if (!flux_prim(Wn, Pn)) return;
+    for (int q = 0; q < 6; ++q) dW[q] = cand[q];
+    for (int q = 0; q < 8; ++q) c.mPc[8 * (size_t)i + q] = Pn[q];
+}
+
+// W~ = W^n + dW~, tau~ and the per-cell record of the micro sweeps: constants of the
+// predicted equilibrium phi~* built from (W~, q^n) (reading: the prediction gives no
+// heat flux, so the last Step-6 value is used), 1/tau~, and 1/dt + 1/tau~.
+template <typename T>
+__global__ void k_macro_finish(Dev<T> c, double cfl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
     double* Wt = c.Wt + 6 * (size_t)i;
     for (int m = 0; m < 6; ++m) Wt[m] = c.W[6 * (size_t)i + m] + c.dW[6 * (size_t)i + m];
     const Prim p = prim_from_W(Wt, c.R);
-    c.taut[i] = relax_time(c, p.rho, p.Ttr);
+    const double tau = relax_time(c, p.rho, p.Ttr);
+    c.taut[i] = tau;
     const double* q = c.q + 6 * (size_t)i;
-    make_eq(c, p.rho, p.U, p.T, p.Ttr, p.Trot, q, q + 3, c.ceq + (size_t)i * EQN);
+    double* e = c.ceq + (size_t)i * CEQ;
+    make_eq(c, p.rho, p.U, p.T, p.Ttr, p.Trot, q, q + 3, e);
+    e[23] = 1.0 / tau;
+    e[24] = 1.0 / (cfl * c.dt[i]) + 1.0 / tau;
 }
 
 // ------------------------------------------------------------------------------------
@@ -706,16 +918,17 @@ __global__ void k_macro_finish(Dev<T> c) {
 //   last sweep  : phi^{n+1} = phi^n + dphi and the sums of Step 6 over k
 // ------------------------------------------------------------------------------------
 template <typename T, int BS>
-__global__ void __launch_bounds__(BS) k_micro_sweep(Dev<T> c, const int* cells, int colour,
-                                                    int first, int first_forward, int last,
-                                                    double cfl) {
-    __shared__ T e[EQN];
-    __shared__ double red[12 * (BS / 32)];
+__global__ void __launch_bounds__(BS, 3) k_micro_sweep(Dev<T> c, const int* cells, int colour,
+                                                    int first, int first_forward, int last) {
+    using R = Red<T>;
+    __shared__ T e[EQN + 2];
+    __shared__ typename R::V red[12 * (BS / 32)];
+    __shared__ double tot[12];
     __shared__ int sh_face[MAXF], sh_nbr[MAXF], sh_ok[MAXF];
     __shared__ T sh_n[3][MAXF], sh_AV[MAXF];
     const int i = cells[blockIdx.x];
     const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
-    if (threadIdx.x < EQN) e[threadIdx.x] = (T)c.ceq[(size_t)i * EQN + threadIdx.x];
+    if (threadIdx.x < EQN + 2) e[threadIdx.x] = (T)c.ceq[(size_t)i * CEQ + threadIdx.x];
     if (threadIdx.x < ns) {
         const int m = s0 + threadIdx.x;
         sh_face[threadIdx.x] = c.slot_face[m];
@@ -728,9 +941,7 @@ __global__ void __launch_bounds__(BS) k_micro_sweep(Dev<T> c, const int* cells, 
         sh_AV[threadIdx.x] = c.slot_AVT[m];
     }
     __syncthreads();
-    const double taud = c.taut[i];
-    const T itau = (T)(1.0 / taud);
-    const T base = (T)(1.0 / (cfl * c.dt[i]) + 1.0 / taud);
+    const T itau = e[EQN - 1], base = e[EQN];
     const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
     const size_t oi = (size_t)i * c.Kp;
     Acc<T> a[12];
@@ -739,9 +950,9 @@ __global__ void __launch_bounds__(BS) k_micro_sweep(Dev<T> c, const int* cells, 
         T rg, rh;
         T D = base, og = T(0), oh = T(0);
         T Fg = T(0), Fh = T(0);
+#pragma unroll 1
         for (int q = 0; q < ns; ++q) {
-            // |u.n| with the face's own normal so that the sign matches the oracle
-            const T un = dot_rn(ux, uy, uz, sh_n[0][q], sh_n[1][q], sh_n[2][q]);
+            const T un = dot_split(ux, uy, uz, sh_n[0][q], sh_n[1][q], sh_n[2][q]);
             const T AV = sh_AV[q];
             if (first) {
                 const size_t of = (size_t)sh_face[q] * c.Kp + k;
@@ -767,7 +978,8 @@ __global__ void __launch_bounds__(BS) k_micro_sweep(Dev<T> c, const int* cells, 
             rg = c.res[oi + k];
             rh = c.res[NK + oi + k];
         }
-        const T dg = (rg - og) / D, dh = (rh - oh) / D;
+        const T iD = T(1) / D;
+        const T dg = (rg - og) * iD, dh = (rh - oh) * iD;
         c.dphi[oi + k] = dg;
         c.dphi[NK + oi + k] = dh;
         if (last) {
@@ -788,50 +1000,57 @@ __global__ void __launch_bounds__(BS) k_micro_sweep(Dev<T> c, const int* cells, 
         }
     }
     if (last) {
-        double v[12];
-        for (int j = 0; j < 12; ++j) v[j] = a[j].get();
-        block_sum<12, BS>(v, red);
-        if (threadIdx.x == 0)
-            for (int j = 0; j < 12; ++j) c.S[(size_t)i * 12 + j] = v[j];
+        typename R::V v[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) v[j] = R::from(a[j]);
+        block_red<T, 12, BS>(v, red, tot);
+        if (threadIdx.x < 12) c.S[(size_t)i * 12 + threadIdx.x] = tot[threadIdx.x];
     }
 }
 
-// Step 6 per cell (compensation) and the residual contributions.
+// Step 6 per cell (compensation) and the residual contributions, summed per block
+// (deterministic) into cellres[block][12].
 template <typename T>
-__global__ void k_cell_update(Dev<T> c) {
+__global__ void __launch_bounds__(128) k_cell_update(Dev<T> c) {
+    __shared__ double red[12 * 4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.N) return;
-    const double Z = c.Z;
-    const double* S = c.S + (size_t)i * 12;
-    const double* Wt = c.Wt + 6 * (size_t)i;
-    double* W = c.W + 6 * (size_t)i;
-    double* q = c.q + 6 * (size_t)i;
-    double Wo[6];
-    for (int m = 0; m < 6; ++m) Wo[m] = W[m];
-    const Prim p = prim_from_W(Wt, c.R);
-    for (int m = 0; m < 5; ++m) W[m] = S[m] + Wt[m];
-    W[5] = S[5] + p.rho * c.R * ((1.0 - 1.0 / Z) * p.Trot + p.T / Z);   // K_rot/2 = 1
-    const double atr = (1.0 / 3.0) * (1.0 - (1.0 - c.omega0) / Z);
-    const double arot = (1.0 - c.delta) * (1.0 - (1.0 - c.omega1) / Z);
-    for (int d = 0; d < 3; ++d) {
-        const double qt = q[d], qr = q[3 + d];
-        q[d] = 0.5 * S[6 + d] + qt * atr;
-        q[3 + d] = S[9 + d] + qr * arot;
+    double r[12];
+    for (int m = 0; m < 12; ++m) r[m] = 0.0;
+    if (i < c.N) {
+        const double Z = c.Z;
+        const double* S = c.S + (size_t)i * 12;
+        const double* Wt = c.Wt + 6 * (size_t)i;
+        double* W = c.W + 6 * (size_t)i;
+        double* q = c.q + 6 * (size_t)i;
+        double Wo[6];
+        for (int m = 0; m < 6; ++m) Wo[m] = W[m];
+        const Prim p = prim_from_W(Wt, c.R);
+        for (int m = 0; m < 5; ++m) W[m] = S[m] + Wt[m];
+        W[5] = S[5] + p.rho * c.R * ((1.0 - 1.0 / Z) * p.Trot + p.T / Z);   // K_rot/2 = 1
+        const double atr = (1.0 / 3.0) * (1.0 - (1.0 - c.omega0) / Z);
+        const double arot = (1.0 - c.delta) * (1.0 - (1.0 - c.omega1) / Z);
+        for (int d = 0; d < 3; ++d) {
+            const double qt = q[d], qr = q[3 + d];
+            q[d] = 0.5 * S[6 + d] + qt * atr;
+            q[3 + d] = S[9 + d] + qr * arot;
+        }
+        for (int m = 0; m < 6; ++m) r[m] = fabs(W[m] - Wo[m]);
+        const double mom = sqrt(Wo[1] * Wo[1] + Wo[2] * Wo[2] + Wo[3] * Wo[3]);
+        r[6] = fabs(Wo[0]); r[7] = mom; r[8] = mom; r[9] = mom; r[10] = fabs(Wo[4]); r[11] = fabs(Wo[5]);
     }
-    double* r = c.cellres + (size_t)i * 12;
-    for (int m = 0; m < 6; ++m) r[m] = fabs(W[m] - Wo[m]);
-    const double mom = sqrt(Wo[1] * Wo[1] + Wo[2] * Wo[2] + Wo[3] * Wo[3]);
-    r[6] = fabs(Wo[0]); r[7] = mom; r[8] = mom; r[9] = mom; r[10] = fabs(Wo[4]); r[11] = fabs(Wo[5]);
+    block_sum<12, 128>(r, red);
+    if (threadIdx.x == 0)
+        for (int m = 0; m < 12; ++m) c.cellres[(size_t)blockIdx.x * 12 + m] = r[m];
 }
 
-// deterministic reduction of the residual contributions (one block of 256)
+// deterministic reduction of the per-block residual partials (one block of 256)
 template <typename T>
-__global__ void __launch_bounds__(256) k_residual_reduce(Dev<T> c) {
+__global__ void __launch_bounds__(256) k_residual_reduce(Dev<T> c, int nblocks) {
     __shared__ double red[12 * 8];
     double v[12];
     for (int j = 0; j < 12; ++j) v[j] = 0.0;
-    for (int i = threadIdx.x; i < c.N; i += 256)
-        for (int j = 0; j < 12; ++j) v[j] += c.cellres[(size_t)i * 12 + j];
+    for (int b = threadIdx.x; b < nblocks; b += 256)
+        for (int j = 0; j < 12; ++j) v[j] += c.cellres[(size_t)b * 12 + j];
     block_sum<12, 256>(v, red);
     if (threadIdx.x == 0) {
         for (int m = 0; m < 6; ++m) c.res12[m] = v[m] / (v[6 + m] > 1e-300 ? v[6 + m] : 1e-300);

@@ -6,6 +6,7 @@
 namespace rk {
 
 constexpr int FACE_BS = 256;
+constexpr int FACE_WPB = 8;         // faces (warps) per block of the interior-face kernel
 constexpr int MICRO_BS = 256;
 constexpr int RECON_BS = 128;
 
@@ -29,9 +30,8 @@ cudaError_t Launch<T>::set_state(const Dev<T>& d, cudaStream_t s, const double* 
 
 template <typename T>
 cudaError_t Launch<T>::recon(const Dev<T>& d, cudaStream_t s, int limiter, Prof& pf) {
-    dim3 grid(d.N, cdiv(d.K, RECON_BS));
     pf.begin(0, s);
-    k_recon<T><<<grid, RECON_BS, 0, s>>>(d, limiter);
+    k_recon<T, RECON_BS><<<d.N, RECON_BS, 0, s>>>(d, limiter);
     pf.end(s);
     pf.launches += 1;
     return cudaGetLastError();
@@ -41,7 +41,7 @@ template <typename T>
 cudaError_t Launch<T>::faces(const Dev<T>& d, cudaStream_t s, Prof& pf) {
     if (d.Fi) {
         pf.begin(1, s);
-        k_face_interior<T, FACE_BS><<<d.Fi, FACE_BS, 0, s>>>(d);
+        k_face_interior<T, FACE_WPB><<<cdiv(d.Fi, FACE_WPB), FACE_WPB * 32, 0, s>>>(d);
         pf.end(s);
         pf.launches += 1;
     }
@@ -68,7 +68,8 @@ template <typename T>
 cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
                              double cfl, Prof& pf) {
     pf.begin(4, s);
-    cudaMemsetAsync(d.dW, 0, sizeof(double) * 6 * (size_t)d.N, s);
+    k_macro_prep<T><<<cdiv(d.N, 128), 128, 0, s>>>(d, cfl);
+    pf.launches += 1;
     const int C = (int)sc.col_off.size() - 1;
     for (int it = 0; it < n_macro; ++it) {
         for (int dir = 0; dir < 2; ++dir) {
@@ -77,12 +78,12 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
                 const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
                 if (!n) continue;
                 k_macro_sweep<T><<<cdiv(n, 128), 128, 0, s>>>(d, sc.col_cell + lo, n, col,
-                                                              it == 0 && dir == 0, cfl);
+                                                              it == 0 && dir == 0);
                 pf.launches += 1;
             }
         }
     }
-    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
+    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d, cfl);
     pf.end(s);
     pf.launches += 1;
     return cudaGetLastError();
@@ -103,14 +104,14 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             // sweep applies the update and the Step-6 sums
             pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
             k_micro_sweep<T, MICRO_BS><<<n, MICRO_BS, 0, s>>>(d, sc.col_cell + lo, col, sw == 0,
-                                                              sw == 0, sw == nsw - 1, cfl);
+                                                              sw == 0, sw == nsw - 1);
             pf.end(s);
             pf.launches += 1;
         }
     }
     pf.begin(8, s);
     k_cell_update<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
-    k_residual_reduce<T><<<1, 256, 0, s>>>(d);
+    k_residual_reduce<T><<<1, 256, 0, s>>>(d, cdiv(d.N, 128));
     pf.end(s);
     pf.launches += 2;
     return cudaGetLastError();
