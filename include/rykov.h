@@ -184,6 +184,36 @@ int rk_profile(rk_ctx* ctx, int enable);
 /* ms[RK_PROF_N], counts[RK_PROF_N + 1] */
 int rk_profile_get(rk_ctx* ctx, double* ms, int64_t* counts);
 
+/* ---- residual without device allocation ------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- for example a convergence monitor or plug-in that runs
+ * inside another framework whose caching allocator owns the device memory (a raw
+ * cudaMalloc there can fail or force a synchronising release), or a check made
+ * every iteration that must not add an allocation or its failure path.
+ *
+ * Computes, on `cuda_stream`, the residual of one implicit step from two states:
+ * res_out[m] = sum_i |W_new[i][m] - W_old[i][m]| / sum_i |W_old[i][m]| for m = rho,
+ * rho E, rho E_rot, and with sum_i |rho U|_i as the denominator of the three
+ * momentum rows -- the same definition as rk_implicit_iterate's res_out.
+ *   W_new, W_old : device pointers, [n_cell][6] doubles (caller-owned inputs)
+ *   res_out      : device pointer, 6 doubles (caller-owned output, written)
+ *   n_cell       : 1 .. RK_NOALLOC_MAX_CELLS, larger sizes return RK_EINVAL
+ * It allocates nothing: its scratch (per-block partial sums, 12 doubles per 256
+ * cells) is one fixed array of RK_NOALLOC_MAX_CELLS / 256 * 12 doubles (384 KiB)
+ * in the library's device memory, which every GPU that loads the library holds
+ * until the process exits.  All calls share that array: calls whose work overlaps
+ * on the GPU (different streams, or devices are fine) race on it and give wrong
+ * results.  Each call overwrites every part of the array it reads, so nothing
+ * carries over from one call to the next.  The first call on a device (with that
+ * device current) looks the array's device address up once; make that first call
+ * before any stream capture.  Returns RK_OK, RK_EINVAL (null pointer, bad size) or
+ * RK_ECUDA; rk_noalloc_last_error() gives the message of the last failed call on
+ * the calling thread.  Asynchronous: the result is ready when the stream reaches it. */
+#define RK_NOALLOC_MAX_CELLS 1048576
+int rk_residual_noalloc(const double* W_new, const double* W_old, int64_t n_cell,
+                        double* res_out, uintptr_t cuda_stream);
+const char* rk_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

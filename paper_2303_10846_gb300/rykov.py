@@ -29,7 +29,8 @@ EXPORTS = ["rk_version", "rk_create", "rk_destroy", "rk_last_error", "rk_upload_
            "rk_upload_dvs", "rk_set_params", "rk_set_bc", "rk_dims", "rk_workspace_size",
            "rk_bind_workspace", "rk_set_state_prim", "rk_set_state", "rk_get_distribution",
            "rk_implicit_iterate", "rk_residual", "rk_moments", "rk_surface", "rk_step",
-           "rk_debug_get", "rk_profile", "rk_profile_get"]
+           "rk_debug_get", "rk_profile", "rk_profile_get", "rk_residual_noalloc",
+           "rk_noalloc_last_error"]
 PROF_CLASSES = ["recon", "face_interior", "face_boundary", "fluxes", "macro_sgs",
                 "micro_sweep_first", "micro_sweep_mid", "micro_sweep_last", "update"]
 
@@ -78,6 +79,8 @@ def load(path: str | None = None):
         "rk_debug_get": ([vp, C.c_int, vp, i64], C.c_int),
         "rk_profile": ([vp, C.c_int], C.c_int),
         "rk_profile_get": ([vp, vp, vp], C.c_int),
+        "rk_residual_noalloc": ([vp, vp, i64, vp, C.c_size_t], C.c_int),
+        "rk_noalloc_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -121,6 +124,13 @@ def rk_create(precision: int, stream: int):
     if rc:
         raise RykovError(rc, "rk_create failed")
     return h
+
+
+def rk_residual_noalloc(W_new, W_old, n_cell: int, res_out, stream: int) -> int:
+    """Residual of one step from two device states into a device output, without
+    any device allocation (see include/rykov.h).  Arguments are CUDA tensors."""
+    return load().rk_residual_noalloc(_ptr(W_new), _ptr(W_old), int(n_cell), _ptr(res_out),
+                                      int(stream))
 
 
 class Solver:
