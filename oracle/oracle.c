@@ -538,14 +538,18 @@ void orc_step_gradient(orc_ctx* c) {
                 if (lim == 2) {
                     L = 0.0;
                 } else if (lim == 1) {
-                    /* limiter at each face centroid, minimum over faces; reading: capped
-                     * at 1 so that it only ever reduces the gradient */
+                    /* limiter at each face centroid, minimum over faces; readings: capped
+                     * at 1 so that it only ever reduces the gradient, and the threshold
+                     * eps^2 = (K V^{1/3})^3 taken relative to the cell value,
+                     * eps^2 phi_i^2, because the distribution spans many orders of
+                     * magnitude (an absolute threshold switches the limiter off in
+                     * near-vacuum cells) */
                     for (int64_t m = c->cf_off[i]; m < c->cf_off[i + 1]; ++m) {
                         int64_t f = c->cf_face[m];
                         const double* xf = c->fx + 3 * f;
                         double r[3] = {xf[0] - xi[0], xf[1] - xi[1], xf[2] - xi[2]};
                         double d2 = dot3(g, r);
-                        double psi = orc_venkat(d2 > 0.0 ? dmax : dmin, d2, c->eps2[i]);
+                        double psi = orc_venkat(d2 > 0.0 ? dmax : dmin, d2, c->eps2[i] * phii * phii);
                         if (psi < L) L = psi;
                     }
                 }

@@ -104,7 +104,7 @@ class Params:
     cfl_imp: float = 1.0e3
     cfl_imp0: float = 0.0     # <= 0: no ramp
     cfl_ramp: float = 1.0
-    lim_k: float = 0.1
+    lim_k: float = 0.3
     n_micro_sgs: int = 2
     n_macro_sgs: int = 40
     limiter: int = 1          # 0 unlimited, 1 Venkatakrishnan, 2 first order

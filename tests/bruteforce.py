@@ -123,7 +123,8 @@ class BruteForce:
                     interior = [r for r, j in zip(dphi, nbrs) if j >= 0]
                     dmax = np.maximum(0.0, np.max(interior, axis=0)) if interior else np.zeros(self.K)
                     dmin = np.minimum(0.0, np.min(interior, axis=0)) if interior else np.zeros(self.K)
-                    eps2 = (P.lim_k * m.cell_volume[i] ** (1.0 / 3.0)) ** 3
+                    # threshold relative to the cell value (per velocity)
+                    eps2 = (P.lim_k * m.cell_volume[i] ** (1.0 / 3.0)) ** 3 * self.phi[fd, i] ** 2
                     L = np.ones(self.K)
                     for f in self.faces_of[i]:
                         d2 = g @ (m.face_center[f] - m.cell_center[i])
