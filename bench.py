@@ -197,24 +197,48 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     clk = Clocks(local_rank)
     clk.start()
-    s.profile(True)
     _, launches0 = s.profile_get()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
     t0 = time.perf_counter()
     e0.record(stream)
-    rc, done, res = s.iterate(args.steps)
+    rc, done, res = s.iterate(args.steps)          # CUDA-graph path
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    prof, launches1 = s.profile_get()
-    s.profile(False)
+    _, launches1 = s.profile_get()
     gpu_launches = launches1 - launches0
+    # per-kernel CUDA-event durations: the same number of steps right after, with
+    # every kernel class bracketed by events on the solver's stream (direct launches)
+    s.profile(True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    s.iterate(args.steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_profiled = p0.elapsed_time(p1) / args.steps
+    prof, _ = s.profile_get()
+    s.profile(False)
     ms = max_over_ranks(ms, world, dev)
     value = job_value(N * K, world, ms)
+
+    # wall time to residual 1e-6 from the initial field (graph path; the residual
+    # is read back every iteration to test convergence)
+    conv = None
+    if args.converge > 0:
+        s.set_state_prim(wl.prim0)
+        barrier()
+        tc = time.perf_counter()
+        rc3, n3, res3 = s.iterate(args.converge, tol=1e-6)
+        torch.cuda.synchronize()
+        tconv = time.perf_counter() - tc
+        conv = {"tol": 1e-6, "iterations": n3, "wall_s": round(tconv, 4),
+                "reached": bool(rc3 == 0 and float(np.max(res3)) < 1e-6),
+                "final_residual": float(np.max(res3))}
 
     # end to end through the public API with host buffers: upload the initial
     # state from pinned host memory, iterate with the residual read back to the
@@ -243,25 +267,35 @@ def run_gpu(args, rank, world, local_rank):
         # the design doc for the per-unit figures)
         F, Fi = wl.mesh.n_face, int((wl.mesh.face_cell[:, 1] >= 0).sum())
         nnz = 2 * Fi + (F - Fi)
-        algo = {
-            "recon": lambda n: (2 * N * K + 2 * F * K) * Tsz,          # read phi, write phi0
-            "face_interior": lambda n: 4 * Fi * K * Tsz,                 # read phi0, write phi_ij
-            "micro_sweep_mid": lambda n: 6 * (N * K) * Tsz / n,          # Res, dphi_j, dphi (per colour launch: N/C cells)
-            "micro_sweep_first": lambda n: (2 * N * K + 2 * nnz * K + 6 * N * K) * Tsz / n,
-            "micro_sweep_last": lambda n: 12 * (N * K) * Tsz / n,
+        # kernels (the micro sweep's first / middle / last launches are one kernel)
+        kern = {
+            "k_recon": prof["recon"], "k_face_interior": prof["face_interior"],
+            "k_face_boundary": prof["face_boundary"], "k_macro (prep + PR-SGS + finish)": prof["macro_sgs"],
+            "k_micro_sweep": tuple(map(sum, zip(prof["micro_sweep_first"], prof["micro_sweep_mid"],
+                                                prof["micro_sweep_last"]))),
         }
-        top = max(prof.items(), key=lambda kv: kv[1][0])
-        name, (tms, cnt) = top
-        per_launch_ms = tms / max(cnt, 1)
+        nsw = 2 * 2                                     # 2 x (forward + backward)
+        # algorithmic words per unit per step: micro 16 + 6 (nsw - 2) + 12
+        # per (cell, k); recon 2 per (cell, k) + 2 per (face, k); faces 4 per (face, k)
+        algo_step = {
+            "k_micro_sweep": (16 + 6 * (nsw - 2) + 12) * N * K * Tsz,
+            "k_recon": (2 * N * K + 2 * F * K) * Tsz,
+            "k_face_interior": 4 * Fi * K * Tsz,
+        }
+        name, (tms, cnt) = max(kern.items(), key=lambda kv: kv[1][0])
         roof = None
-        if name in algo and cnt:
-            # launches per step of that class
-            per_step = cnt / args.steps
-            bytes_launch = algo[name](per_step) if name.startswith("micro") else algo[name](1)
-            ach = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+        if name in algo_step and cnt:
+            launches_per_step = cnt / args.steps
+            bytes_launch = algo_step[name] / launches_per_step
+            ach = bytes_launch / (tms / cnt * 1e-3) / 1e9
             roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
-                    "peak_kind": peak_kind, "share_of_step": round(tms / (ms * args.steps), 4)}
+                    "peak_kind": peak_kind, "launches_per_step": launches_per_step,
+                    "algorithmic_bytes_per_launch": int(bytes_launch),
+                    "share_of_step": round(tms / (ms_profiled * args.steps), 4),
+                    "timing": "CUDA events around every launch of the kernel on the solver "
+                              "stream, in a profiled pass of the same number of steps run "
+                              "right after the timed (graph) region"}
         # whole iteration against the 52-word per (cell, velocity) model
         iter_bytes = 52 * Tsz * N * K
         cpu_v, cores, sample = cpu_oracle_rate(wl) if not args.no_cpu else (None, 0, "skipped")
@@ -283,6 +317,8 @@ def run_gpu(args, rank, world, local_rank):
                                    "achieved": round(iter_bytes / (ms * 1e-3) / 1e9, 1),
                                    "peak": peak, "frac": round(iter_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+            "ms_per_step_profiled": round(ms_profiled, 3),
+            "time_to_residual": conv,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "residual_after": float(np.max(res)),
@@ -301,6 +337,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--start", type=int, default=START_ITERS)
+    ap.add_argument("--converge", type=int, default=600,
+                    help="iteration cap of the time-to-residual-1e-6 run (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

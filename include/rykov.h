@@ -67,7 +67,7 @@ typedef struct rk_params {
     double cfl_imp;     /* implicit step = cfl * Delta t_i: the largest cfl       */
     double cfl_imp0;    /* cfl of the first iteration after set_state (<=0: none) */
     double cfl_ramp;    /* geometric growth of cfl per iteration                  */
-    double lim_k;       /* Venkatakrishnan constant K, eps^2 = (K V^{1/3})^3      */
+    double lim_k;       /* Venkatakrishnan K: eps^2 = (K V^{1/3})^3 phi_i^2 (relative) */
     int32_t n_micro_sgs;   /* PR-SGS iterations of Eq. implicit_mic_final_equ (2) */
     int32_t n_macro_sgs;   /* PR-SGS iterations of Eq. implicit_mac_equ_fin (40)  */
     int32_t limiter;       /* 0 unlimited, 1 Venkatakrishnan, 2 first order       */

@@ -3,7 +3,9 @@
 // colour schedule, carves every device array out of the caller's workspace, and
 // enqueues the kernel sequence of one implicit iteration on the caller's stream.
 #include <cmath>
+#include <type_traits>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -68,6 +70,13 @@ struct rk_ctx {
     double* pin = nullptr;                            // pinned host: 16 doubles
     int64_t iter = 0;
     bool have_state = false;
+    // CUDA graph of one implicit iteration (captured on a private stream, launched on
+    // the caller's stream); rebuilt after anything baked into it changes
+    bool use_graph = true;
+    bool use_coop = false;            // cooperative launch of the macro PR-SGS (RYKOV_COOP=1)
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;
     double last_res[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -99,6 +108,10 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     if (!ctx) return RK_ENOMEM;
     ctx->prec = base;
     ctx->debug = (precision & RK_DEBUG_FLAG) != 0;
+    // RYKOV_GRAPH=0 switches off the CUDA graph of an iteration, RYKOV_COOP=1 switches
+    // on the cooperative macro solve (same results; used to compare launch schemes)
+    if (const char* v = std::getenv("RYKOV_GRAPH")) ctx->use_graph = std::strcmp(v, "0") != 0;
+    if (const char* v = std::getenv("RYKOV_COOP")) ctx->use_coop = std::strcmp(v, "0") != 0;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
     std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
@@ -120,6 +133,8 @@ extern "C" int rk_destroy(rk_ctx* ctx) {
     if (!ctx) return RK_EINVAL;
     if (ctx->pin) cudaFreeHost(ctx->pin);
     for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
     return RK_OK;
 }
@@ -135,6 +150,10 @@ extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
     bool geo_change = ctx->p.cfl_s != p->cfl_s || ctx->p.lim_k != p->lim_k;
     ctx->p = *p;
     ctx->have_params = true;
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
     if (ctx->bound && geo_change) {
         ctx->dd.cfl_s = ctx->df.cfl_s = p->cfl_s;
         ctx->dd.lim_k = ctx->df.lim_k = p->lim_k;
@@ -143,6 +162,11 @@ extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
         d.R = p->R; d.Z = p->Z_rot; d.omega_vis = p->omega_vis; d.mu_ref = p->mu_ref;
         d.T_ref = p->T_ref; d.omega0 = p->omega0; d.omega1 = p->omega1; d.delta = p->delta;
         d.cfl_s = p->cfl_s; d.lim_k = p->lim_k;
+        d.cfl_imp = p->cfl_imp; d.cfl_imp0 = p->cfl_imp0; d.cfl_ramp = p->cfl_ramp;
+        d.first_order_iters = p->first_order_iters; d.limiter = p->limiter;
+        using TT = std::remove_reference_t<decltype(d.tp[0])>;
+        const double v[8] = {p->R, p->Z_rot, p->mu_ref, p->T_ref, p->omega_vis, p->omega0, p->omega1, p->delta};
+        for (int j = 0; j < 8; ++j) d.tp[j] = (TT)v[j];
     };
     fill(ctx->dd);
     fill(ctx->df);
@@ -312,6 +336,9 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.fc = cv.take<int>(2 * F); d.fn = cv.take<double>(3 * F); d.fa = cv.take<double>(F);
     d.fxc = cv.take<double>(3 * F); d.fs = cv.take<double>(F); d.fdl = cv.take<double>(F);
     d.rf = cv.take<double>(F);
+    d.fnT = cv.take<T>(3 * F); d.fsT = cv.take<T>(F);
+    d.iterp = cv.take<double>(4);
+    d.debug = ctx->debug ? 1 : 0;
     d.face_int = cv.take<int>(ctx->Fi + 1); d.face_bnd = cv.take<int>(ctx->Fb + 1);
     d.bcv = cv.take<double>(MAX_BC * 5); d.bck = cv.take<int>(MAX_BC);
     d.u = cv.take<double>(3 * Kp); d.w = cv.take<double>(Kp);
@@ -326,6 +353,8 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.cellres = cv.take<double>(12 * N); d.res12 = cv.take<double>(16);
     d.mPc = cv.take<double>(8 * N); d.mDb = cv.take<double>(4 * N);
     d.sG0 = cv.take<double>(6 * nnz); d.sC = cv.take<double>(2 * nnz);
+    d.bar = cv.take<unsigned int>(4);
+    d.col_off_d = cv.take<int>(ctx->C + 1);
     d.status = cv.take<int>(4);
     int* col_cell = cv.take<int>(N);
     ctx->sched.col_cell = col_cell;
@@ -397,13 +426,29 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
     CK(h2d(d.uT, uTs.data(), 3 * Kp * sizeof(T)));
     CK(h2d(d.wT, wTs.data(), Kp * sizeof(T)));
     CK(h2d(ctx->sched.col_cell, ctx->col_cell.data(), N * 4));
+    CK(h2d(d.col_off_d, ctx->col_off.data(), (ctx->C + 1) * 4));
+    CK(cudaMemsetAsync(d.bar, 0, 4 * sizeof(unsigned int), s));
     ctx->sched.col_off = ctx->col_off;
+    {
+        // cooperative macro solve: one co-resident grid of up to 2 blocks per SM
+        int dev = 0, sms = 0, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        const int per = std::min(2, rk::Launch<T>::coop_blocks_per_sm());
+        ctx->sched.coop_grid = (coop && per > 0 && ctx->use_coop) ? sms * per : 0;
+    }
     // zero the distribution-sized arrays once so that the K padding stays 0
     CK(cudaMemsetAsync(d.phi, 0, 2 * N * Kp * sizeof(T), s));
     CK(cudaMemsetAsync(d.face, 0, 2 * F * Kp * sizeof(T), s));
     CK(cudaMemsetAsync(d.res, 0, 2 * N * Kp * sizeof(T), s));
     CK(cudaMemsetAsync(d.dphi, 0, 2 * N * Kp * sizeof(T), s));
     CK(cudaMemsetAsync(d.status, 0, 4 * sizeof(int), s));
+    CK(cudaMemsetAsync(d.iterp, 0, 4 * sizeof(double), s));
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
     CK(cudaMemsetAsync(d.wallq, 0, 8 * (size_t)(ctx->Fb + 1) * 8, s));
     CK(cudaMemsetAsync(d.fstate, 0, rk::FST * F * 8, s));
     cudaError_t e = rk::Launch<T>::setup(d, s);
@@ -448,6 +493,7 @@ static int set_state_prim_impl(rk_ctx* ctx, rk::Dev<T>& d, const double* prim, c
     }
     cudaError_t e = rk::Launch<T>::set_state(d, ctx->stream, pd, qd);
     if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+    CK(cudaMemsetAsync(d.iterp, 0, 4 * sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->iter = 0;
     ctx->have_state = true;
@@ -481,6 +527,8 @@ extern "C" int rk_set_state(rk_ctx* ctx, const double* W, const double* q, const
     if (q) CK(cudaMemcpyAsync(dq, q, 6 * N * 8, kind, ctx->stream));
     else CK(cudaMemsetAsync(dq, 0, 6 * N * 8, ctx->stream));
     CK(cudaMemcpyAsync(dphi, dist, 2 * N * Kp * tsz, kind, ctx->stream));
+    CK(cudaMemsetAsync(ctx->prec == RK_FP64 ? (void*)ctx->dd.iterp : (void*)ctx->df.iterp, 0,
+                       4 * sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->iter = 0;
     ctx->have_state = true;
@@ -498,26 +546,75 @@ extern "C" int rk_get_distribution(rk_ctx* ctx, void* dist, int on_device) {
     return RK_OK;
 }
 
-// one step of the iteration (see RK_STEP_*)
+// one step of the iteration (see RK_STEP_*), launched on stream s
+template <typename T>
+static cudaError_t launch_step(rk_ctx* ctx, rk::Dev<T>& d, int step, cudaStream_t s) {
+    switch (step) {
+        case RK_STEP_RECON: return rk::Launch<T>::recon(d, s, ctx->prof);
+        case RK_STEP_FACES: return rk::Launch<T>::faces(d, s, ctx->prof);
+        case RK_STEP_FLUXES: return rk::Launch<T>::fluxes(d, s, ctx->prof);
+        case RK_STEP_MACRO: return rk::Launch<T>::macro(d, s, ctx->sched, ctx->p.n_macro_sgs, ctx->prof);
+        case RK_STEP_MICRO: return rk::Launch<T>::micro(d, s, ctx->sched, ctx->p.n_micro_sgs, ctx->prof);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T>
 static int step_impl(rk_ctx* ctx, rk::Dev<T>& d, int step) {
-    cudaError_t e = cudaSuccess;
-    const int limiter = ctx->iter < ctx->p.first_order_iters ? 2 : ctx->p.limiter;
-    const double cfl = implicit_cfl(ctx->p, ctx->iter);
-    switch (step) {
-        case RK_STEP_RECON: e = rk::Launch<T>::recon(d, ctx->stream, limiter, ctx->prof); break;
-        case RK_STEP_FACES: e = rk::Launch<T>::faces(d, ctx->stream, ctx->prof); break;
-        case RK_STEP_FLUXES: e = rk::Launch<T>::fluxes(d, ctx->stream, ctx->prof); break;
-        case RK_STEP_MACRO:
-            e = rk::Launch<T>::macro(d, ctx->stream, ctx->sched, ctx->p.n_macro_sgs, cfl, ctx->prof);
-            break;
-        case RK_STEP_MICRO:
-            e = rk::Launch<T>::micro(d, ctx->stream, ctx->sched, ctx->p.n_micro_sgs, cfl, ctx->prof);
-            ctx->iter++;
-            break;
-        default: return fail(ctx, RK_EINVAL, "rk_step: unknown step");
-    }
+    if (step < RK_STEP_RECON || step > RK_STEP_MICRO) return fail(ctx, RK_EINVAL, "rk_step: unknown step");
+    cudaError_t e = launch_step(ctx, d, step, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, RK_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (step == RK_STEP_MICRO) ctx->iter++;
+    return RK_OK;
+}
+
+// capture one whole iteration into a CUDA graph (on a private stream)
+template <typename T>
+static int build_graph(rk_ctx* ctx, rk::Dev<T>& d) {
+    if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    const bool pon = ctx->prof.on;
+    const long long l0 = ctx->prof.launches;
+    ctx->prof.on = false;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int st = RK_STEP_RECON; st <= RK_STEP_MICRO && e == cudaSuccess; ++st) e = launch_step(ctx, d, st, ctx->cap);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
+    ctx->graph_kernels = ctx->prof.launches - l0;
+    ctx->prof.launches = l0;
+    ctx->prof.on = pon;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, RK_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        ctx->gexec = nullptr;
+        return fail(ctx, RK_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    }
+    return RK_OK;
+}
+
+// one whole iteration: the captured graph, or direct launches while profiling
+template <typename T>
+static int iteration(rk_ctx* ctx, rk::Dev<T>& d) {
+    if (ctx->use_graph && !ctx->prof.on) {
+        if (!ctx->gexec && build_graph(ctx, d) != RK_OK) {
+            // capture not available for this sequence: direct launches from now on
+            ctx->use_graph = false;
+            (void)cudaGetLastError();
+        } else {
+            CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            ctx->prof.launches += ctx->graph_kernels;
+            ctx->iter++;
+            return RK_OK;
+        }
+    }
+    for (int st = RK_STEP_RECON; st <= RK_STEP_MICRO; ++st) {
+        int rc = step_impl(ctx, d, st);
+        if (rc) return rc;
+    }
     return RK_OK;
 }
 
@@ -527,6 +624,9 @@ static int read_residual(rk_ctx* ctx, rk::Dev<T>& d) {
     CK(cudaMemcpyAsync(ctx->pin + 8, d.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (int m = 0; m < 6; ++m) ctx->last_res[m] = ctx->pin[m];
+    int status = 0;
+    std::memcpy(&status, ctx->pin + 8, sizeof(int));
+    if (status & 4) return fail(ctx, RK_ETIMEOUT, "macro PR-SGS: a grid barrier wait gave up");
     return RK_OK;
 }
 
@@ -535,8 +635,7 @@ static int iterate_impl(rk_ctx* ctx, rk::Dev<T>& d, int32_t n_iter, double tol, 
     int32_t it = 0;
     int rc = RK_OK;
     for (; it < n_iter; ++it) {
-        for (int st = RK_STEP_RECON; st <= RK_STEP_MICRO; ++st)
-            if ((rc = step_impl(ctx, d, st))) return rc;
+        if ((rc = iteration(ctx, d))) return rc;
         if (tol > 0.0 || it == n_iter - 1) {
             if ((rc = read_residual(ctx, d))) return rc;
             bool bad = false;
@@ -613,8 +712,7 @@ extern "C" int rk_moments(rk_ctx* ctx, double* W, double* q, double* T3, int on_
 template <typename T>
 static int surface_impl(rk_ctx* ctx, rk::Dev<T>& d, double rho_inf, const double* U_inf, double T_inf,
                         double* per, double force[3], double* heat) {
-    const int limiter = ctx->iter < ctx->p.first_order_iters ? 2 : ctx->p.limiter;
-    cudaError_t e = rk::Launch<T>::recon(d, ctx->stream, limiter, ctx->prof);
+    cudaError_t e = rk::Launch<T>::recon(d, ctx->stream, ctx->prof);
     if (e == cudaSuccess) e = rk::Launch<T>::faces(d, ctx->stream, ctx->prof);
     const double U2 = U_inf[0] * U_inf[0] + U_inf[1] * U_inf[1] + U_inf[2] * U_inf[2];
     const double qd = 0.5 * rho_inf * U2;

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace rk {
 
 constexpr int MAXF = 8;        // faces per cell
@@ -23,6 +25,13 @@ constexpr double PI = 3.14159265358979323846;
 template <typename T>
 struct Dev {
     int N, F, K, Kp, C, Fi, Fb, nnz;
+    int debug;                         // write verification-only records (face states)
+    // R, Z, mu_ref, T_ref, omega_vis, omega0, omega1, delta in T (no conversions in kernels)
+    T tp[8];
+    // implicit-step schedule, evaluated on the device each iteration (k_iter_begin)
+    double cfl_imp, cfl_imp0, cfl_ramp;
+    int first_order_iters, limiter;
+    double* iterp;                     // [0] cfl, [1] limiter, [2] iteration counter
     // gas / scheme parameters
     double R, Z, omega_vis, mu_ref, T_ref, omega0, omega1, delta, cfl_s, lim_k;
     // cells
@@ -40,6 +49,7 @@ struct Dev {
     const int* fc;                     // [F][2]
     const double *fn, *fa, *fxc;       // [3][F], [F], [3][F]
     double *fs, *fdl, *rf;             // s_ij, distance used in r_ij, r_ij  [F]
+    T *fnT, *fsT;                      // face normal [3][F] and s_ij [F] in T
     const int *face_int, *face_bnd;    // lists
     const double* bcv;                 // [64][5]: rho, U, T
     const int* bck;                    // [64] kind
@@ -54,6 +64,8 @@ struct Dev {
     // current iterate per cell, diagonal base per cell, per-slot Euler flux of the
     // neighbour's W^n and the coefficients A/(2V), A r/(2V)
     double *mPc, *mDb, *sG0, *sC;        // mDb: [N][4] = 1/D, 1/(D + 1/(Z tau)), 1/(Z tau)
+    unsigned int* bar;                   // grid-barrier state of the cooperative macro solve
+    const int* col_off_d;                // colour offsets on the device (C + 1)
     int* status;
 };
 
@@ -78,8 +90,13 @@ __device__ __forceinline__ double dot_split(double ax, double ay, double az, dou
 __device__ __forceinline__ float dot_split(float ax, float ay, float az, float bx, float by, float bz) {
     return fmaf(az, bz, fmaf(ay, by, ax * bx));
 }
+// exp of the per-velocity arithmetic: FP64 exp in FP64 mode; the hardware exp2-based
+// __expf in mixed mode (relative error ~1e-6 over the arguments that matter, below
+// the 1e-5 target of the mixed mode)
 __device__ __forceinline__ double ex(double x) { return exp(x); }
-__device__ __forceinline__ float ex(float x) { return expf(x); }
+__device__ __forceinline__ float ex(float x) { return __expf(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 
 // Accumulators for sums over the velocity space.  FP64 mode: plain FP64 sum.  Mixed
 // mode: Kahan-compensated FP32 sum (every operation rounded as written), combined in
@@ -133,6 +150,9 @@ struct Red<double> {
     static __device__ __forceinline__ V add(V a, V b) { return a + b; }
     static __device__ __forceinline__ V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     static __device__ __forceinline__ double to_d(V v) { return v; }
+    static __device__ __forceinline__ double to_T(V v) { return v; }
+    static __device__ __forceinline__ void store(double* p, V v) { *p = v; }
+    static __device__ __forceinline__ double load(const double* p) { return *p; }
 };
 template <>
 struct Red<float> {
@@ -144,6 +164,15 @@ struct Red<float> {
         return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
     }
     static __device__ __forceinline__ double to_d(V v) { return (double)v.hi + (double)v.lo; }
+    static __device__ __forceinline__ float to_T(V v) { return __fadd_rn(v.hi, v.lo); }
+    // a double slot holds the float-float pair (hi, lo)
+    static __device__ __forceinline__ void store(double* p, V v) {
+        *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo);
+    }
+    static __device__ __forceinline__ double load(const double* p) {
+        const float2 x = *reinterpret_cast<const float2*>(p);
+        return (double)x.x + (double)x.y;
+    }
 };
 
 template <typename T, int NV>
@@ -221,6 +250,37 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
     __syncthreads();
 }
 
+// Per-lane vector width of the velocity loops: two consecutive velocities (8-byte
+// loads) in mixed mode, one in FP64 mode.  Rows are padded to 32 velocities, so the
+// vector accesses never leave a row and stay aligned.
+template <typename T>
+struct VW;
+template <>
+struct VW<float> {
+    static constexpr int N = 2;
+};
+template <>
+struct VW<double> {
+    static constexpr int N = 1;
+};
+__device__ __forceinline__ void vload(const float* p, float (&x)[2]) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+}
+__device__ __forceinline__ void vload(const float* p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ __forceinline__ void vstore(float* p, const float (&x)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void vload(const double* p, double (&x)[1]) { x[0] = *p; }
+__device__ __forceinline__ void vstore(float* p, const float (&x)[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+}
+__device__ __forceinline__ void vstore(double* p, const double (&x)[1]) { *p = x[0]; }
+
 // ------------------------------------------------------------------------------------
 // gas model
 // ------------------------------------------------------------------------------------
@@ -255,10 +315,23 @@ __device__ __forceinline__ Prim prim_from_W(const double* W, double R) {
 //  11 1/(15 R T_tr p_tr)  12 1/(R T_tr)  13 rho (2 pi R T)^-1.5  14 1/(2 R T)
 //  15 omega0/(15 R T p)  16 1/(R T)  17 R T_rot  18 R T  19 (1-delta)/(R T_tr p_rot)
 //  20 omega1 (1-delta)/(R T p)  21 1 - 1/Z  22 1/Z
+// gas parameter j (0 R, 1 Z, 2 mu_ref, 3 T_ref, 4 omega_vis, 5 omega0, 6 omega1,
+// 7 delta) in arithmetic type S
+template <typename S, typename T>
+__device__ __forceinline__ S par(const Dev<T>& c, int j) {
+    if constexpr (std::is_same<S, T>::value) {
+        return c.tp[j];
+    } else {
+        const double v[8] = {c.R, c.Z, c.mu_ref, c.T_ref, c.omega_vis, c.omega0, c.omega1, c.delta};
+        return (S)v[j];
+    }
+}
+
 template <typename T, typename S>
 __device__ void make_eq(const Dev<T>& c, S rho, const S* U, S Tq, S Ttr, S Trot, const S* qtr,
                         const S* qrot, S* e) {
-    const S R = (S)c.R;
+    const S R = par<S>(c, 0), Z = par<S>(c, 1), om0 = par<S>(c, 5), om1 = par<S>(c, 6),
+            del = par<S>(c, 7);
     const S RTtr = R * Ttr, RT = R * Tq, RTrot = R * Trot;
     const S ptr = rho * RTtr, p = rho * RT, prot = rho * RTrot;
     for (int d = 0; d < 3; ++d) { e[d] = U[d]; e[3 + d] = qtr[d]; e[6 + d] = qrot[d]; }
@@ -270,14 +343,14 @@ __device__ void make_eq(const Dev<T>& c, S rho, const S* U, S Tq, S Ttr, S Trot,
     const S b = S(2.0 * PI) * RT;
     e[13] = rho / (b * sqrt(b));
     e[14] = S(1) / (S(2) * RT);
-    e[15] = (S)c.omega0 / (S(15) * RT * p);
+    e[15] = om0 / (S(15) * RT * p);
     e[16] = S(1) / RT;
     e[17] = RTrot;
     e[18] = RT;
-    e[19] = (S(1) - (S)c.delta) / (RTtr * prot);
-    e[20] = (S)c.omega1 * (S(1) - (S)c.delta) / (RT * p);
-    e[21] = S(1) - S(1) / (S)c.Z;
-    e[22] = S(1) / (S)c.Z;
+    e[19] = (S(1) - del) / (RTtr * prot);
+    e[20] = om1 * (S(1) - del) / (RT * p);
+    e[21] = S(1) - S(1) / Z;
+    e[22] = S(1) / Z;
 }
 
 template <typename T>
@@ -401,6 +474,10 @@ __global__ void k_setup_face(Dev<T> c) {
 template <typename T>
 __global__ void k_setup_slotT(Dev<T> c) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < c.F) {
+        c.fsT[m] = (T)c.fs[m];
+        for (int r = 0; r < 3; ++r) c.fnT[r * c.F + m] = (T)c.fn[r * c.F + m];
+    }
     if (m >= c.nnz) return;
     c.slot_AVT[m] = (T)c.slot_AV[m];
     c.slot_sT[m] = (T)c.fs[c.slot_face[m]];
@@ -450,79 +527,120 @@ __global__ void k_set_state(Dev<T> c, const double* prim, const double* qin) {
 // cell, velocities strided over the block; the cell's face data staged in shared
 // memory.
 // ------------------------------------------------------------------------------------
-template <typename T, int BS>
-__global__ void __launch_bounds__(BS, 6) k_recon(Dev<T> c, int limiter) {
-    __shared__ int s_face[MAXF], s_nbr[MAXF], s_left[MAXF];
-    __shared__ T s_lsq[3][MAXF], s_d[3][MAXF], s_n[3][MAXF], s_s[MAXF];
-    const int i = blockIdx.x;
+template <typename T, int WPB>
+__global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
+    constexpr int NV = VW<T>::N;
+    __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_left[WPB][MAXF];
+    __shared__ T s_lsq[WPB][3][MAXF], s_d[WPB][3][MAXF], s_n[WPB][3][MAXF], s_s[WPB][MAXF];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * WPB + w;
+    if (i >= c.N) return;                         // whole warp
     const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
-    if (threadIdx.x < ns) {
-        const int m = s0 + threadIdx.x, q = threadIdx.x;
-        s_face[q] = c.slot_face[m];
-        s_nbr[q] = c.slot_nbr[m];
-        s_left[q] = c.slot_left[m];
-        s_s[q] = c.slot_sT[m];
+    if (lane < ns) {
+        const int m = s0 + lane;
+        s_face[w][lane] = c.slot_face[m];
+        s_nbr[w][lane] = c.slot_nbr[m];
+        s_left[w][lane] = c.slot_left[m];
+        s_s[w][lane] = c.slot_sT[m];
         for (int r = 0; r < 3; ++r) {
-            s_lsq[r][q] = c.slot_lsqT[r * c.nnz + m];
-            s_d[r][q] = c.slot_dT[r * c.nnz + m];
-            s_n[r][q] = c.slot_nT[r * c.nnz + m];
+            s_lsq[w][r][lane] = c.slot_lsqT[r * c.nnz + m];
+            s_d[w][r][lane] = c.slot_dT[r * c.nnz + m];
+            s_n[w][r][lane] = c.slot_nT[r * c.nnz + m];
         }
     }
-    __syncthreads();
+    __syncwarp();
     const T eps2 = (T)c.eps2[i];
+    const int limiter = (int)c.iterp[1];
     const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
     const T* phg = c.phi + (size_t)i * c.Kp;
     const T* phh = c.phi + NK + (size_t)i * c.Kp;
-    for (int k = threadIdx.x; k < c.K; k += BS) {
-        const T pg = phg[k], ph = phh[k];
-        T g[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
-        T dmax[2] = {T(0), T(0)}, dmin[2] = {T(0), T(0)};
+    for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+        T pg[NV], ph[NV];
+        vload(phg + k0, pg);
+        vload(phh + k0, ph);
+        T g[2][3][NV], dmax[2][NV], dmin[2][NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e)
+            for (int fd = 0; fd < 2; ++fd) {
+                g[fd][0][e] = g[fd][1][e] = g[fd][2][e] = T(0);
+                dmax[fd][e] = dmin[fd][e] = T(0);
+            }
 #pragma unroll 1
         for (int q = 0; q < ns; ++q) {
-            const int j = s_nbr[q];
+            const int j = s_nbr[w][q];
             if (j < 0) continue;
-            const T dg = c.phi[(size_t)j * c.Kp + k] - pg;
-            const T dh = c.phi[NK + (size_t)j * c.Kp + k] - ph;
-            const T lx = s_lsq[0][q], ly = s_lsq[1][q], lz = s_lsq[2][q];
-            g[0][0] += lx * dg; g[0][1] += ly * dg; g[0][2] += lz * dg;
-            g[1][0] += lx * dh; g[1][1] += ly * dh; g[1][2] += lz * dh;
-            dmax[0] = dg > dmax[0] ? dg : dmax[0]; dmin[0] = dg < dmin[0] ? dg : dmin[0];
-            dmax[1] = dh > dmax[1] ? dh : dmax[1]; dmin[1] = dh < dmin[1] ? dh : dmin[1];
+            T xg[NV], xh[NV];
+            vload(c.phi + (size_t)j * c.Kp + k0, xg);
+            vload(c.phi + NK + (size_t)j * c.Kp + k0, xh);
+            const T lx = s_lsq[w][0][q], ly = s_lsq[w][1][q], lz = s_lsq[w][2][q];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                const T dg = xg[e] - pg[e], dh = xh[e] - ph[e];
+                g[0][0][e] += lx * dg; g[0][1][e] += ly * dg; g[0][2][e] += lz * dg;
+                g[1][0][e] += lx * dh; g[1][1][e] += ly * dh; g[1][2][e] += lz * dh;
+                dmax[0][e] = dg > dmax[0][e] ? dg : dmax[0][e]; dmin[0][e] = dg < dmin[0][e] ? dg : dmin[0][e];
+                dmax[1][e] = dh > dmax[1][e] ? dh : dmax[1][e]; dmin[1][e] = dh < dmin[1][e] ? dh : dmin[1][e];
+            }
         }
-        T L[2] = {T(1), T(1)};
-        if (limiter == 2) {
-            L[0] = L[1] = T(0);
-        } else if (limiter == 1) {
+        T L[2][NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) L[0][e] = L[1][e] = (limiter == 2) ? T(0) : T(1);
+        if (limiter == 1) {
             // min over faces of Venkatakrishnan's psi = num/den, kept as a fraction
-            // (den > 0) so that only the minimum is divided; capped at 1 (reading)
-            T bn[2] = {T(1), T(1)}, bd[2] = {T(1), T(1)};
+            // (den > 0) so that only the minimum is divided; capped at 1, threshold
+            // eps^2 phi_i^2 relative to the cell value (readings)
+            T bn[2][NV], bd[2][NV];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) bn[0][e] = bn[1][e] = bd[0][e] = bd[1][e] = T(1);
 #pragma unroll 1
             for (int q = 0; q < ns; ++q) {
-                const T dx = s_d[0][q], dy = s_d[1][q], dz = s_d[2][q];
+                const T dx = s_d[w][0][q], dy = s_d[w][1][q], dz = s_d[w][2][q];
 #pragma unroll
-                for (int fd = 0; fd < 2; ++fd) {
-                    const T d2 = g[fd][0] * dx + g[fd][1] * dy + g[fd][2] * dz;
-                    if (d2 == T(0)) continue;
-                    const T d1 = d2 > T(0) ? dmax[fd] : dmin[fd];
-                    const T num = d1 * d1 + eps2 + T(2) * d1 * d2;
-                    const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + eps2;
-                    if (num * bd[fd] < bn[fd] * den) { bn[fd] = num; bd[fd] = den; }
-                }
+                for (int e = 0; e < NV; ++e)
+#pragma unroll
+                    for (int fd = 0; fd < 2; ++fd) {
+                        const T d2 = g[fd][0][e] * dx + g[fd][1][e] * dy + g[fd][2][e] * dz;
+                        if (d2 == T(0)) continue;
+                        const T d1 = d2 > T(0) ? dmax[fd][e] : dmin[fd][e];
+                        const T ph0 = fd == 0 ? pg[e] : ph[e];
+                        const T ep = eps2 * ph0 * ph0;      // threshold relative to the cell value
+                        const T num = d1 * d1 + ep + T(2) * d1 * d2;
+                        const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
+                        if (num * bd[fd][e] < bn[fd][e] * den) { bn[fd][e] = num; bd[fd][e] = den; }
+                    }
             }
-            L[0] = bn[0] / bd[0];
-            L[1] = bn[1] / bd[1];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) { L[0][e] = bn[0][e] / bd[0][e]; L[1][e] = bn[1][e] / bd[1][e]; }
         }
-        const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k];
+        T ux[NV], uy[NV], uz[NV];
+        vload(c.uT + k0, ux);
+        vload(c.uT + c.Kp + k0, uy);
+        vload(c.uT + 2 * c.Kp + k0, uz);
 #pragma unroll 1
         for (int q = 0; q < ns; ++q) {
-            const T un = dot_rn(ux, uy, uz, s_n[0][q], s_n[1][q], s_n[2][q]);
-            const bool up = s_left[q] ? (un > T(0)) : (un <= T(0));
-            if (!up) continue;
-            const T sq = s_s[q];
-            const T rx = s_d[0][q] - ux * sq, ry = s_d[1][q] - uy * sq, rz = s_d[2][q] - uz * sq;
-            const size_t o = (size_t)s_face[q] * c.Kp + k;
-            c.face[o] = pg + L[0] * (g[0][0] * rx + g[0][1] * ry + g[0][2] * rz);
-            c.face[FK + o] = ph + L[1] * (g[1][0] * rx + g[1][1] * ry + g[1][2] * rz);
+            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+            const T sq = s_s[w][q], dx = s_d[w][0][q], dy = s_d[w][1][q], dz = s_d[w][2][q];
+            const bool left = s_left[w][q];
+            const size_t o = (size_t)s_face[w][q] * c.Kp + k0;
+            T vg[NV], vh[NV];
+            bool up[NV], all = true;
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                const T un = dot_rn(ux[e], uy[e], uz[e], nx, ny, nz);
+                up[e] = left ? (un > T(0)) : (un <= T(0));
+                all = all && up[e];
+                const T rx = dx - ux[e] * sq, ry = dy - uy[e] * sq, rz = dz - uz[e] * sq;
+                vg[e] = pg[e] + L[0][e] * (g[0][0][e] * rx + g[0][1][e] * ry + g[0][2][e] * rz);
+                vh[e] = ph[e] + L[1][e] * (g[1][0][e] * rx + g[1][1][e] * ry + g[1][2][e] * rz);
+            }
+            if (all) {
+                vstore(c.face + o, vg);
+                vstore(c.face + FK + o, vh);
+            } else {
+#pragma unroll
+                for (int e = 0; e < NV; ++e)
+                    if (up[e]) { c.face[o + e] = vg[e]; c.face[FK + o + e] = vh[e]; }
+            }
         }
     }
 }
@@ -565,7 +683,13 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
     for (int d = 0; d < 3; ++d) Ur[d] = __shfl_sync(0xffffffffu, Ur[d], 0);
     V v[17];
     {
-        Acc<T> m[17];
+        // compensated: the conserved moments (0-4); plain per-lane FP32 sums (<= K/32
+        // terms each, then float-float across lanes): the second and third moments,
+        // which only enter the heat-flux correction
+        Acc<T> m[5];
+        T p2[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) p2[j] = T(0);
         for (int k = lane; k < c.K; k += 32) {
             const T cx = c.uT[k] - Ur[0], cy = c.uT[c.Kp + k] - Ur[1], cz = c.uT[2 * c.Kp + k] - Ur[2];
             const T w = c.wT[k];
@@ -573,14 +697,20 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
             m[0].add(wg);
             m[1].add(wg * cx); m[2].add(wg * cy); m[3].add(wg * cz);
             m[4].add(wh);
-            m[5].add(wg * cx * cx); m[6].add(wg * cy * cy); m[7].add(wg * cz * cz);
-            m[8].add(wg * cx * cy); m[9].add(wg * cx * cz); m[10].add(wg * cy * cz);
+            p2[0] += wg * cx * cx; p2[1] += wg * cy * cy; p2[2] += wg * cz * cz;
+            p2[3] += wg * cx * cy; p2[4] += wg * cx * cz; p2[5] += wg * cy * cz;
             const T wgc2 = wg * (cx * cx + cy * cy + cz * cz);
-            m[11].add(wgc2 * cx); m[12].add(wgc2 * cy); m[13].add(wgc2 * cz);
-            m[14].add(wh * cx); m[15].add(wh * cy); m[16].add(wh * cz);
+            p2[6] += wgc2 * cx; p2[7] += wgc2 * cy; p2[8] += wgc2 * cz;
+            p2[9] += wh * cx; p2[10] += wh * cy; p2[11] += wh * cz;
         }
 #pragma unroll
-        for (int j = 0; j < 17; ++j) v[j] = R::from(m[j]);
+        for (int j = 0; j < 5; ++j) v[j] = R::from(m[j]);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            Acc<T> t;
+            t.add(p2[j]);
+            v[5 + j] = R::from(t);
+        }
     }
     warp_red<T, 17>(v);
     // interface state on lane 0, in the per-velocity arithmetic type T (the moments
@@ -591,8 +721,8 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
     for (int j = 0; j < NB; ++j) cst[j] = T(0);
     if (lane == 0) {
         T x[17];
-        for (int j = 0; j < 17; ++j) x[j] = (T)R::to_d(v[j]);
-        const T Rg = (T)c.R, Z = (T)c.Z, s = (T)c.fs[f];
+        for (int j = 0; j < 17; ++j) x[j] = (T)R::to_T(v[j]);
+        const T Rg = par<T>(c, 0), Z = par<T>(c, 1), s = c.fsT[f];
         const T rho = x[0];
         const T d[3] = {x[1] / rho, x[2] / rho, x[3] / rho};
         const T U[3] = {Ur[0] + d[0], Ur[1] + d[1], Ur[2] + d[2]};
@@ -604,7 +734,7 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
         // tau from the translational temperature of the free-transport moments
         // (reading of the circular definition of the interface tau)
         const T Ttr0 = etr / (T(1.5) * rho * Rg);
-        const T tau = (T)c.mu_ref * pow(Ttr0 / (T)c.T_ref, (T)c.omega_vis) / (rho * Rg * Ttr0);
+        const T tau = par<T>(c, 2) * pow(Ttr0 / par<T>(c, 3), par<T>(c, 4)) / (rho * Rg * Ttr0);
         const T Erot = (Z * tau * Er0 + s * rho * Rg * Tq) / (Z * tau + s);
         const T Trot = Erot / (rho * Rg);
         const T Ttr = (etr + Er0 - Erot) / (T(1.5) * rho * Rg);
@@ -612,8 +742,8 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
         const T Sd[3] = {x[5] * d[0] + x[8] * d[1] + x[9] * d[2],
                          x[8] * d[0] + x[6] * d[1] + x[10] * d[2],
                          x[9] * d[0] + x[10] * d[1] + x[7] * d[2]};
-        const T dtr = tau + s - s / T(3) * (T(1) - T(1) / Z + (T)c.omega0 / Z);
-        const T drot = tau + s - s * (T(1) - (T)c.delta) * (T(1) - T(1) / Z + (T)c.omega1 / Z);
+        const T dtr = tau + s - s / T(3) * (T(1) - T(1) / Z + par<T>(c, 5) / Z);
+        const T drot = tau + s - s * (T(1) - par<T>(c, 7)) * (T(1) - T(1) / Z + par<T>(c, 6) / Z);
         T qtr[3], qrot[3];
         for (int k = 0; k < 3; ++k) {
             const T Qtr = x[11 + k] - T(2) * Sd[k] - tr * d[k] + T(2) * rho * dd * d[k];
@@ -623,16 +753,18 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
         make_eq(c, rho, U, Tq, Ttr, Trot, qtr, qrot, cst + 2);
         cst[0] = tau / (tau + s);
         cst[1] = s / (tau + s);
-        double* st = c.fstate + (size_t)f * FST;
-        st[0] = rho; st[1] = U[0]; st[2] = U[1]; st[3] = U[2];
-        st[4] = Tq; st[5] = Ttr; st[6] = Trot; st[7] = tau;
-        for (int k = 0; k < 3; ++k) { st[8 + k] = qtr[k]; st[11 + k] = qrot[k]; }
-        st[14] = s; st[15] = 0.0;
+        if (c.debug) {
+            double* st = c.fstate + (size_t)f * FST;
+            st[0] = rho; st[1] = U[0]; st[2] = U[1]; st[3] = U[2];
+            st[4] = Tq; st[5] = Ttr; st[6] = Trot; st[7] = tau;
+            for (int k = 0; k < 3; ++k) { st[8 + k] = qtr[k]; st[11 + k] = qrot[k]; }
+            st[14] = c.fs[f]; st[15] = 0.0;
+        }
     }
     T e[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) e[j] = __shfl_sync(0xffffffffu, cst[j], 0);
-    const T nx = (T)c.fn[f], ny = (T)c.fn[c.F + f], nz = (T)c.fn[2 * c.F + f];
+    const T nx = c.fnT[f], ny = c.fnT[c.F + f], nz = c.fnT[2 * c.F + f];
     const T a = e[0], b = e[1];
     V r6[6];
     {
@@ -656,7 +788,7 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
     }
     warp_red<T, 6>(r6);
     if (lane == 0)
-        for (int d = 0; d < 6; ++d) c.mface[(size_t)f * 6 + d] = R::to_d(r6[d]);
+        for (int d = 0; d < 6; ++d) R::store(c.mface + (size_t)f * 6 + d, r6[d]);
 }
 
 // Boundary faces (reading; the paper names diffuse reflection but gives no formula):
@@ -734,7 +866,14 @@ __global__ void __launch_bounds__(BS) k_face_boundary(Dev<T> c) {
     }
     block_sum<7, BS>(v, red);
     if (threadIdx.x == 0) {
-        for (int d = 0; d < 6; ++d) c.mface[(size_t)f * 6 + d] = v[d];
+        for (int d = 0; d < 6; ++d) {
+            if (sizeof(T) == 8) {
+                c.mface[(size_t)f * 6 + d] = v[d];
+            } else {
+                const float hi = (float)v[d];
+                *reinterpret_cast<float2*>(c.mface + (size_t)f * 6 + d) = make_float2(hi, (float)(v[d] - (double)hi));
+            }
+        }
         double* wq = c.wallq + 8 * (size_t)b;
         wq[0] = v[6];                                // p_w
         wq[1] = v[1]; wq[2] = v[2]; wq[3] = v[3];    // sum w (u.n) u G
@@ -776,7 +915,7 @@ __global__ void k_cell_macro_flux(Dev<T> c) {
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
         const int f = c.slot_face[m];
         const double sg = c.slot_left[m] ? 1.0 : -1.0;
-        for (int d = 0; d < 6; ++d) M[d] += sg * c.fa[f] * c.mface[6 * (size_t)f + d];
+        for (int d = 0; d < 6; ++d) M[d] += sg * c.fa[f] * Red<T>::load(c.mface + 6 * (size_t)f + d);
     }
     const double iv = 1.0 / c.vol[i];
     for (int d = 0; d < 6; ++d) c.macroF[6 * (size_t)i + d] = M[d] * iv;
@@ -812,10 +951,26 @@ __device__ __forceinline__ bool flux_prim(const double* W, double* P) {
 // value: reading of the tilde quantities in the source), 1/(Z tau); per slot the
 // neighbour's Euler flux G_ij(W_j^n) and the coefficients A/(2V), A r/(2V); the flux
 // primitives of W^n; dW~ = 0.
+// implicit-step factor and reconstruction order of the current iteration:
+// cfl = min(cfl_imp, cfl_imp0 cfl_ramp^n) (cfl_imp if no ramp), first order for
+// n < first_order_iters (readings of the unspecified implicit step and start-up)
 template <typename T>
-__global__ void k_macro_prep(Dev<T> c, double cfl) {
+__global__ void k_iter_begin(Dev<T> c) {
+    const double n = c.iterp[2];
+    double cfl = c.cfl_imp;
+    if (c.cfl_imp0 > 0.0 && c.cfl_ramp > 1.0) {
+        const double r = c.cfl_imp0 * pow(c.cfl_ramp, n);
+        cfl = r < c.cfl_imp ? r : c.cfl_imp;
+    }
+    c.iterp[0] = cfl;
+    c.iterp[1] = (n < (double)c.first_order_iters) ? 2.0 : (double)c.limiter;
+}
+
+template <typename T>
+__global__ void k_macro_prep(Dev<T> c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
+    const double cfl = c.iterp[0];
     const double iv = 1.0 / c.vol[i];
     double D = 1.0 / (cfl * c.dt[i]);
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
@@ -832,6 +987,7 @@ __global__ void k_macro_prep(Dev<T> c, double cfl) {
     }
     const Prim p = prim_from_W(c.W + 6 * (size_t)i, c.R);
     const double izt = 1.0 / (c.Z * relax_time(c, p.rho, p.Ttr));
+    if (i == 0) c.bar[0] = 0u;            // arrival count of the cooperative solve
     c.mDb[4 * (size_t)i] = 1.0 / D;
     c.mDb[4 * (size_t)i + 1] = 1.0 / (D + izt);
     c.mDb[4 * (size_t)i + 2] = izt;
@@ -847,11 +1003,7 @@ __global__ void k_macro_prep(Dev<T> c, double cfl) {
 // An update whose predicted state is not admissible (rho, T_tr or T_rot not
 // positive) is skipped.
 template <typename T>
-__global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* cells, int n, int colour,
-                                                     int first_forward) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int i = cells[t];
+__device__ __forceinline__ void macro_point(const Dev<T>& c, int i, int colour, int first_forward) {
     double o[6] = {0, 0, 0, 0, 0, 0};
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
         const int j = c.slot_nbr[m];
@@ -859,23 +1011,31 @@ __global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* cells,
         const int f = c.slot_face[m];
         const double sg = c.slot_left[m] ? 1.0 : -1.0;
         const double nx = sg * c.fn[f], ny = sg * c.fn[c.F + f], nz = sg * c.fn[2 * c.F + f];
-        const double* P = c.mPc + 8 * (size_t)j;
+        // the iterate of neighbours is read through L2: in the cooperative solve it was
+        // written by other blocks during this kernel
+        double P[8], dWj[6];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) P[q] = __ldcg(c.mPc + 8 * (size_t)j + q);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) dWj[q] = __ldcg(c.dW + 6 * (size_t)j + q);
         const double Un = P[1] * nx + P[2] * ny + P[3] * nz;
         const double rU = P[0] * Un;
         const double G1[6] = {rU, rU * P[1] + P[5] * nx, rU * P[2] + P[5] * ny, rU * P[3] + P[5] * nz,
                               P[4] * Un, P[6] * Un};
         const double* G0 = c.sG0 + 6 * (size_t)m;
-        const double* dWj = c.dW + 6 * (size_t)j;
         const double c1 = c.sC[2 * (size_t)m], c2 = c.sC[2 * (size_t)m + 1];
 #pragma unroll
         for (int q = 0; q < 6; ++q) o[q] += c1 * (G1[q] - G0[q]) - c2 * dWj[q];
     }
     const double* W = c.W + 6 * (size_t)i;
     double* dW = c.dW + 6 * (size_t)i;
+    double dWi[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) dWi[q] = __ldcg(dW + q);
     // rho R T of the current iterate: (2/5)(rho E - |rho U|^2 / (2 rho))
-    const double rc = W[0] + dW[0];
-    const double mx = W[1] + dW[1], my = W[2] + dW[2], mz = W[3] + dW[3];
-    const double rRT = 0.4 * (W[4] + dW[4] - 0.5 * (mx * mx + my * my + mz * mz) / rc);
+    const double rc = W[0] + dWi[0];
+    const double mx = W[1] + dWi[1], my = W[2] + dWi[2], mz = W[3] + dWi[3];
+    const double rRT = 0.4 * (W[4] + dWi[4] - 0.5 * (mx * mx + my * my + mz * mz) / rc);
     const double* F = c.macroF + 6 * (size_t)i;
     const double iD = c.mDb[4 * (size_t)i], iDr = c.mDb[4 * (size_t)i + 1], izt = c.mDb[4 * (size_t)i + 2];
     double cand[6];
@@ -884,17 +1044,83 @@ __global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* cells,
     double Wn[6], Pn[8];
     for (int q = 0; q < 6; ++q) Wn[q] = W[q] + cand[q];
     if (!flux_prim(Wn, Pn)) return;
-    for (int q = 0; q < 6; ++q) dW[q] = cand[q];
-    for (int q = 0; q < 8; ++q) c.mPc[8 * (size_t)i + q] = Pn[q];
+    for (int q = 0; q < 6; ++q) __stcg(dW + q, cand[q]);
+    for (int q = 0; q < 8; ++q) __stcg(c.mPc + 8 * (size_t)i + q, Pn[q]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* cells, int n, int colour,
+                                                     int first_forward) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    macro_point(c, cells[t], colour, first_forward);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The wait is
+// bounded: after one second without the barrier opening the block records status
+// bit 4 and stops waiting (every other block then stops at its next wait), so a
+// failure returns RK_ETIMEOUT to the host instead of hanging the GPU.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if ((*(volatile int*)status & 4) || global_ns() - t0 > 1000000000ull) {
+                    atomicOr(status, 4);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !(*(volatile int*)status & 4);
+}
+
+// All n_macro x (forward + backward) colour sweeps of the macro PR-SGS in one
+// cooperative launch; the cells of a colour are strided over the grid, colours are
+// separated by grid barriers.  Same order and arithmetic as k_macro_sweep.
+template <typename T>
+__global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cell, const int* col_off,
+                                                    int C, int n_macro, unsigned int* bar) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int it = 0; it < n_macro; ++it) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int cc = 0; cc < C; ++cc) {
+                const int col = dir == 0 ? cc : C - 1 - cc;
+                const int lo = col_off[col], hi = col_off[col + 1];
+                const int ff = (it == 0 && dir == 0);
+                for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += stride)
+                    macro_point(c, col_cell[t], col, ff);
+                if (!grid_barrier(bar, c.status)) return;
+            }
+        }
+    }
 }
 
 // W~ = W^n + dW~, tau~ and the per-cell record of the micro sweeps: constants of the
 // predicted equilibrium phi~* built from (W~, q^n) (reading: the prediction gives no
 // heat flux, so the last Step-6 value is used), 1/tau~, and 1/dt + 1/tau~.
 template <typename T>
-__global__ void k_macro_finish(Dev<T> c, double cfl) {
+__global__ void k_macro_finish(Dev<T> c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
+    const double cfl = c.iterp[0];
     double* Wt = c.Wt + 6 * (size_t)i;
     for (int m = 0; m < 6; ++m) Wt[m] = c.W[6 * (size_t)i + m] + c.dW[6 * (size_t)i + m];
     const Prim p = prim_from_W(Wt, c.R);
@@ -917,94 +1143,146 @@ __global__ void k_macro_finish(Dev<T> c, double cfl) {
 //                 D = 1/dt + 1/tau~ + sum_f (A/V) max(u.n, 0); boundary ghosts 0
 //   last sweep  : phi^{n+1} = phi^n + dphi and the sums of Step 6 over k
 // ------------------------------------------------------------------------------------
-template <typename T, int BS>
-__global__ void __launch_bounds__(BS, 3) k_micro_sweep(Dev<T> c, const int* cells, int colour,
-                                                    int first, int first_forward, int last) {
+// FIRST (forms Res; the first sweep is the forward one) and LAST (update and Step-6
+// sums) are separate instantiations, so that the middle sweeps carry neither the
+// face reads nor the twelve accumulators
+template <typename T, int WPB, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? 2 : (FIRST ? 3 : 4)))
+    k_micro_sweep(Dev<T> c, const int* cells, int ncells, int colour) {
+    constexpr bool first = FIRST, last = LAST, first_forward = FIRST;
     using R = Red<T>;
-    __shared__ T e[EQN + 2];
-    __shared__ typename R::V red[12 * (BS / 32)];
-    __shared__ double tot[12];
-    __shared__ int sh_face[MAXF], sh_nbr[MAXF], sh_ok[MAXF];
-    __shared__ T sh_n[3][MAXF], sh_AV[MAXF];
-    const int i = cells[blockIdx.x];
+    // velocities per lane: 16-byte accesses in the middle sweeps of the mixed mode
+    constexpr int NV = (sizeof(T) == 4 && !FIRST && !LAST) ? 4 : VW<T>::N;
+    __shared__ T s_e[WPB][EQN + 2];
+    __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_ok[WPB][MAXF];
+    __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * WPB + w;
+    if (t >= ncells) return;                      // whole warp: no block barriers below
+    const int i = cells[t];
     const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
-    if (threadIdx.x < EQN + 2) e[threadIdx.x] = (T)c.ceq[(size_t)i * CEQ + threadIdx.x];
-    if (threadIdx.x < ns) {
-        const int m = s0 + threadIdx.x;
-        sh_face[threadIdx.x] = c.slot_face[m];
-        sh_nbr[threadIdx.x] = c.slot_nbr[m];
-        sh_ok[threadIdx.x] = (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour);
+    if (lane < EQN + 2) s_e[w][lane] = (T)c.ceq[(size_t)i * CEQ + lane];
+    if (lane < ns) {
+        const int m = s0 + lane;
+        s_face[w][lane] = c.slot_face[m];
+        s_nbr[w][lane] = c.slot_nbr[m];
+        s_ok[w][lane] = (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour);
         const T sg = c.slot_left[m] ? T(1) : T(-1);
-        sh_n[0][threadIdx.x] = sg * c.slot_nT[m];
-        sh_n[1][threadIdx.x] = sg * c.slot_nT[c.nnz + m];
-        sh_n[2][threadIdx.x] = sg * c.slot_nT[2 * c.nnz + m];
-        sh_AV[threadIdx.x] = c.slot_AVT[m];
+        s_n[w][0][lane] = sg * c.slot_nT[m];
+        s_n[w][1][lane] = sg * c.slot_nT[c.nnz + m];
+        s_n[w][2][lane] = sg * c.slot_nT[2 * c.nnz + m];
+        s_AV[w][lane] = c.slot_AVT[m];
     }
-    __syncthreads();
+    __syncwarp();
+    const T* e = s_e[w];
     const T itau = e[EQN - 1], base = e[EQN];
     const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
     const size_t oi = (size_t)i * c.Kp;
     Acc<T> a[12];
-    for (int k = threadIdx.x; k < c.K; k += BS) {
-        const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k];
-        T rg, rh;
-        T D = base, og = T(0), oh = T(0);
-        T Fg = T(0), Fh = T(0);
+    for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+        T ux[NV], uy[NV], uz[NV];
+        vload(c.uT + k0, ux);
+        vload(c.uT + c.Kp + k0, uy);
+        vload(c.uT + 2 * c.Kp + k0, uz);
+        T D[NV], og[NV], oh[NV], Fg[NV], Fh[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { D[q] = base; og[q] = oh[q] = Fg[q] = Fh[q] = T(0); }
 #pragma unroll 1
         for (int q = 0; q < ns; ++q) {
-            const T un = dot_split(ux, uy, uz, sh_n[0][q], sh_n[1][q], sh_n[2][q]);
-            const T AV = sh_AV[q];
+            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q], AV = s_AV[w][q];
+            T un[NV];
+            bool neg = false;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                un[v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
+                neg = neg || !(un[v] > T(0));
+            }
             if (first) {
-                const size_t of = (size_t)sh_face[q] * c.Kp + k;
-                Fg += AV * un * c.face[of];
-                Fh += AV * un * c.face[FK + of];
+                T fg[NV], fh[NV];
+                const size_t of = (size_t)s_face[w][q] * c.Kp + k0;
+                vload(c.face + of, fg);
+                vload(c.face + FK + of, fh);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { Fg[v] += AV * un[v] * fg[v]; Fh[v] += AV * un[v] * fh[v]; }
             }
-            if (un > T(0)) {
-                D += AV * un;
-            } else if (sh_ok[q]) {
-                const size_t oj = (size_t)sh_nbr[q] * c.Kp + k;
-                og += AV * un * c.dphi[oj];
-                oh += AV * un * c.dphi[NK + oj];
+            T dg[NV], dh[NV];
+            const bool ok = s_ok[w][q] && neg;
+            if (ok) {
+                const size_t oj = (size_t)s_nbr[w][q] * c.Kp + k0;
+                vload(c.dphi + oj, dg);
+                vload(c.dphi + NK + oj, dh);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if (un[v] > T(0)) {
+                    D[v] += AV * un[v];
+                } else if (ok) {
+                    og[v] += AV * un[v] * dg[v];
+                    oh[v] += AV * un[v] * dh[v];
+                }
             }
         }
-        T G = T(0), H = T(0);
-        if (first || last) eval_eq(e, ux, uy, uz, G, H);
+        T G[NV], H[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            G[v] = H[v] = T(0);
+            if (first || last) eval_eq(e, ux[v], uy[v], uz[v], G[v], H[v]);
+        }
+        T rg[NV], rh[NV], pg[NV], ph[NV];
+        if (first || last) {
+            vload(c.phi + oi + k0, pg);
+            vload(c.phi + NK + oi + k0, ph);
+        }
         if (first) {
-            rg = (G - c.phi[oi + k]) * itau - Fg;
-            rh = (H - c.phi[NK + oi + k]) * itau - Fh;
-            c.res[oi + k] = rg;
-            c.res[NK + oi + k] = rh;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                rg[v] = (G[v] - pg[v]) * itau - Fg[v];
+                rh[v] = (H[v] - ph[v]) * itau - Fh[v];
+            }
+            vstore(c.res + oi + k0, rg);
+            vstore(c.res + NK + oi + k0, rh);
         } else {
-            rg = c.res[oi + k];
-            rh = c.res[NK + oi + k];
+            vload(c.res + oi + k0, rg);
+            vload(c.res + NK + oi + k0, rh);
         }
-        const T iD = T(1) / D;
-        const T dg = (rg - og) * iD, dh = (rh - oh) * iD;
-        c.dphi[oi + k] = dg;
-        c.dphi[NK + oi + k] = dh;
+        T xg[NV], xh[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const T iD = rcp(D[v]);
+            xg[v] = (rg[v] - og[v]) * iD;
+            xh[v] = (rh[v] - oh[v]) * iD;
+        }
+        vstore(c.dphi + oi + k0, xg);
+        vstore(c.dphi + NK + oi + k0, xh);
         if (last) {
-            const T g1 = c.phi[oi + k] + dg, h1 = c.phi[NK + oi + k] + dh;
-            c.phi[oi + k] = g1;
-            c.phi[NK + oi + k] = h1;
-            const T w = c.wT[k];
-            const T Dg = g1 - G, Dh = h1 - H;
-            const T cx = ux - e[0], cy = uy - e[1], cz = uz - e[2];
-            const T c2 = cx * cx + cy * cy + cz * cz;
-            const T wg = w * Dg, wh = w * Dh;
-            a[0].add(wg); a[1].add(wg * ux); a[2].add(wg * uy); a[3].add(wg * uz);
-            a[4].add(T(0.5) * (ux * ux + uy * uy + uz * uz) * wg + wh);
-            a[5].add(wh);
-            const T wgc = wg * c2;
-            a[6].add(wgc * cx); a[7].add(wgc * cy); a[8].add(wgc * cz);
-            a[9].add(wh * cx); a[10].add(wh * cy); a[11].add(wh * cz);
+            T g1[NV], h1[NV], wv[NV];
+            vload(c.wT + k0, wv);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                g1[v] = pg[v] + xg[v];
+                h1[v] = ph[v] + xh[v];
+                const T Dg = g1[v] - G[v], Dh = h1[v] - H[v];
+                const T cx = ux[v] - e[0], cy = uy[v] - e[1], cz = uz[v] - e[2];
+                const T c2 = cx * cx + cy * cy + cz * cz;
+                const T wg = wv[v] * Dg, wh = wv[v] * Dh;
+                a[0].add(wg); a[1].add(wg * ux[v]); a[2].add(wg * uy[v]); a[3].add(wg * uz[v]);
+                a[4].add(T(0.5) * (ux[v] * ux[v] + uy[v] * uy[v] + uz[v] * uz[v]) * wg + wh);
+                a[5].add(wh);
+                const T wgc = wg * c2;
+                a[6].add(wgc * cx); a[7].add(wgc * cy); a[8].add(wgc * cz);
+                a[9].add(wh * cx); a[10].add(wh * cy); a[11].add(wh * cz);
+            }
+            vstore(c.phi + oi + k0, g1);
+            vstore(c.phi + NK + oi + k0, h1);
         }
     }
     if (last) {
         typename R::V v[12];
 #pragma unroll
         for (int j = 0; j < 12; ++j) v[j] = R::from(a[j]);
-        block_red<T, 12, BS>(v, red, tot);
-        if (threadIdx.x < 12) c.S[(size_t)i * 12 + threadIdx.x] = tot[threadIdx.x];
+        warp_red<T, 12>(v);
+        if (lane == 0)
+            for (int j = 0; j < 12; ++j) c.S[(size_t)i * 12 + j] = R::to_d(v[j]);
     }
 }
 
@@ -1057,6 +1335,7 @@ __global__ void __launch_bounds__(256) k_residual_reduce(Dev<T> c, int nblocks) 
         int bad = 0;
         for (int m = 0; m < 6; ++m) bad |= !isfinite(c.res12[m]);
         if (bad) atomicOr(c.status, 2);
+        c.iterp[2] += 1.0;              // end of the implicit iteration
     }
 }
 

@@ -36,6 +36,7 @@ struct Prof {
 struct Sched {
     const int* col_cell;            // device: cells grouped by colour
     std::vector<int> col_off;       // host: colour offsets (C+1)
+    int coop_grid = 0;              // blocks of the cooperative macro solve (0: per-colour launches)
 };
 
 template <typename T>
@@ -43,15 +44,16 @@ struct Launch {
     static cudaError_t setup(const Dev<T>& d, cudaStream_t s);
     static cudaError_t set_state(const Dev<T>& d, cudaStream_t s, const double* prim,
                                  const double* q);
-    static cudaError_t recon(const Dev<T>& d, cudaStream_t s, int limiter, Prof& pf);
+    static cudaError_t recon(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t faces(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
-                             double cfl, Prof& pf);
+                             Prof& pf);
     static cudaError_t micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,
-                             double cfl, Prof& pf);
+                             Prof& pf);
     static cudaError_t debug_micro_flux(const Dev<T>& d, cudaStream_t s, T* out);
     static cudaError_t temps(const Dev<T>& d, cudaStream_t s, double* out);
+    static int coop_blocks_per_sm();
     static cudaError_t surface(const Dev<T>& d, cudaStream_t s, const int* wall_b, int nw,
                                double p_inf, double qdyn, double Umag, double* out,
                                double* contrib, double* tot);

@@ -7,8 +7,8 @@ namespace rk {
 
 constexpr int FACE_BS = 256;
 constexpr int FACE_WPB = 8;         // faces (warps) per block of the interior-face kernel
-constexpr int MICRO_BS = 256;
-constexpr int RECON_BS = 128;
+constexpr int MICRO_WPB = 8;        // cells (warps) per block of the micro sweep
+constexpr int RECON_WPB = 8;        // cells (warps) per block of the reconstruction
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -17,7 +17,7 @@ cudaError_t Launch<T>::setup(const Dev<T>& d, cudaStream_t s) {
     k_setup_dt<T><<<d.N, 128, 0, s>>>(d);
     k_setup_lsq<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
     k_setup_face<T><<<cdiv(d.F, 256), 256, 0, s>>>(d);
-    k_setup_slotT<T><<<cdiv(d.nnz, 256), 256, 0, s>>>(d);
+    k_setup_slotT<T><<<cdiv(d.nnz > d.F ? d.nnz : d.F, 256), 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -29,11 +29,12 @@ cudaError_t Launch<T>::set_state(const Dev<T>& d, cudaStream_t s, const double* 
 }
 
 template <typename T>
-cudaError_t Launch<T>::recon(const Dev<T>& d, cudaStream_t s, int limiter, Prof& pf) {
+cudaError_t Launch<T>::recon(const Dev<T>& d, cudaStream_t s, Prof& pf) {
+    k_iter_begin<T><<<1, 1, 0, s>>>(d);
     pf.begin(0, s);
-    k_recon<T, RECON_BS><<<d.N, RECON_BS, 0, s>>>(d, limiter);
+    k_recon<T, RECON_WPB><<<cdiv(d.N, RECON_WPB), RECON_WPB * 32, 0, s>>>(d);
     pf.end(s);
-    pf.launches += 1;
+    pf.launches += 2;
     return cudaGetLastError();
 }
 
@@ -66,12 +67,32 @@ cudaError_t Launch<T>::fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf) {
 
 template <typename T>
 cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
-                             double cfl, Prof& pf) {
+                             Prof& pf) {
     pf.begin(4, s);
-    k_macro_prep<T><<<cdiv(d.N, 128), 128, 0, s>>>(d, cfl);
+    k_macro_prep<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
     pf.launches += 1;
     const int C = (int)sc.col_off.size() - 1;
-    for (int it = 0; it < n_macro; ++it) {
+    bool done = false;
+    if (sc.coop_grid > 0 && n_macro > 0) {
+        // all sweeps in one cooperative launch (grid barriers between colours)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(sc.coop_grid);
+        cfg.blockDim = dim3(128);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_macro_coop<T>, d, sc.col_cell, d.col_off_d, C, n_macro, d.bar);
+        if (e == cudaSuccess) {
+            pf.launches += 1;
+            done = true;
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
+    for (int it = 0; it < n_macro && !done; ++it) {
         for (int dir = 0; dir < 2; ++dir) {
             for (int cc = 0; cc < C; ++cc) {
                 const int col = dir == 0 ? cc : C - 1 - cc;
@@ -83,7 +104,7 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             }
         }
     }
-    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d, cfl);
+    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
     pf.end(s);
     pf.launches += 1;
     return cudaGetLastError();
@@ -91,7 +112,7 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
 
 template <typename T>
 cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,
-                             double cfl, Prof& pf) {
+                             Prof& pf) {
     const int C = (int)sc.col_off.size() - 1;
     const int nsw = 2 * n_micro;
     for (int sw = 0; sw < nsw; ++sw) {
@@ -103,8 +124,13 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             // the first sweep forms Res for every cell of this colour; the last
             // sweep applies the update and the Step-6 sums
             pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
-            k_micro_sweep<T, MICRO_BS><<<n, MICRO_BS, 0, s>>>(d, sc.col_cell + lo, col, sw == 0,
-                                                              sw == 0, sw == nsw - 1);
+            const dim3 g(cdiv(n, MICRO_WPB)), b(MICRO_WPB * 32);
+            if (sw == 0)
+                k_micro_sweep<T, MICRO_WPB, true, false><<<g, b, 0, s>>>(d, sc.col_cell + lo, n, col);
+            else if (sw == nsw - 1)
+                k_micro_sweep<T, MICRO_WPB, false, true><<<g, b, 0, s>>>(d, sc.col_cell + lo, n, col);
+            else
+                k_micro_sweep<T, MICRO_WPB, false, false><<<g, b, 0, s>>>(d, sc.col_cell + lo, n, col);
             pf.end(s);
             pf.launches += 1;
         }
@@ -122,6 +148,13 @@ cudaError_t Launch<T>::debug_micro_flux(const Dev<T>& d, cudaStream_t s, T* out)
     dim3 grid(d.N, cdiv(d.K, 128));
     k_debug_micro_flux<T><<<grid, 128, 0, s>>>(d, out);
     return cudaGetLastError();
+}
+
+template <typename T>
+int Launch<T>::coop_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_macro_coop<T>, 128, 0) != cudaSuccess) return 0;
+    return n;
 }
 
 template <typename T>
