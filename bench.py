@@ -34,6 +34,10 @@ if ROOT not in sys.path:
 METRIC = "cell-velocity updates/s per implicit sweep; wall time to residual 1e-6"
 UNIT = "cell-velocity updates/s"
 START_ITERS = 10          # start-up iterations (first order, CFL ramp), untimed
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
+# as they stand, mixed precision, full sphere workload: one ncu capture on the same mesh
+# with every 5th velocity (K = 607), scaled by 3033/607 (traffic is proportional to K)
+NCU_TRAFFIC_MIXED = {"k_micro_sweep": 1.598e9, "k_recon": 4.700e9, "k_face_interior": 5.667e9}
 
 
 def _peaks():
@@ -127,6 +131,7 @@ def dvs_sample(wl, stride):
     w2 = copy.copy(wl)
     w2.dvs = I.DVS(u=wl.dvs.u[::stride].copy(), w=wl.dvs.w[::stride] * stride,
                    name=f"{wl.dvs.name}/every{stride}")
+    w2.name = f"{wl.name}/every{stride}thvelocity_K{w2.dvs.K}"
     return w2
 
 
@@ -182,6 +187,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     wl = workload()
+    if args.kstride > 1:
+        wl = dvs_sample(wl, args.kstride)
     N, K = wl.mesh.n_cell, wl.dvs.K
     s = Solver(wl, args.precision)
     stream = s.stream
@@ -289,7 +296,9 @@ def run_gpu(args, rank, world, local_rank):
             bytes_launch = algo_step[name] / launches_per_step
             ach = bytes_launch / (tms / cnt * 1e-3) / 1e9
             roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(ach / peak, 4),
+                    "traffic": (NCU_TRAFFIC_MIXED.get(name) if args.precision == "mixed"
+                                and args.kstride == 1 else None),
                     "peak_kind": peak_kind, "launches_per_step": launches_per_step,
                     "algorithmic_bytes_per_launch": int(bytes_launch),
                     "share_of_step": round(tms / (ms_profiled * args.steps), 4),
@@ -339,6 +348,9 @@ def main():
     ap.add_argument("--start", type=int, default=START_ITERS)
     ap.add_argument("--converge", type=int, default=600,
                     help="iteration cap of the time-to-residual-1e-6 run (0: skip)")
+    ap.add_argument("--kstride", type=int, default=1,
+                    help="keep every S-th velocity (weights x S): the smaller case that "
+                         "profiler captures of single kernels run on; not a bench line")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
