@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 BUF_PHI, BUF_W, BUF_Q, BUF_GRAD, BUF_FACE, BUF_FACE0, BUF_FSTATE, BUF_MICRO_F, \
-    BUF_MACRO_F, BUF_WT, BUF_RES, BUF_DPHI, BUF_DT, BUF_S, BUF_TAUT = range(15)
+    BUF_MACRO_F, BUF_WT, BUF_RES, BUF_DPHI, BUF_DT, BUF_S, BUF_TAUT, BUF_LSTORE = range(16)
 
 
 class OrcParams(C.Structure):
@@ -34,7 +34,8 @@ class OrcParams(C.Structure):
                 ("cfl_imp", C.c_double), ("cfl_imp0", C.c_double), ("cfl_ramp", C.c_double),
                 ("lim_k", C.c_double),
                 ("n_micro_sgs", C.c_int32), ("n_macro_sgs", C.c_int32),
-                ("limiter", C.c_int32), ("first_order_iters", C.c_int32)]
+                ("limiter", C.c_int32), ("first_order_iters", C.c_int32),
+                ("limiter_freeze", C.c_int32)]
 
 
 class OrcState(C.Structure):
@@ -247,7 +248,7 @@ class Oracle:
         BUF_MICRO_F: lambda s: (2, s.N, s.K), BUF_MACRO_F: lambda s: (s.N, 6),
         BUF_WT: lambda s: (s.N, 6), BUF_RES: lambda s: (2, s.N, s.K),
         BUF_DPHI: lambda s: (2, s.N, s.K), BUF_DT: lambda s: (s.N, 3), BUF_S: lambda s: (s.F,),
-        BUF_TAUT: lambda s: (s.N,),
+        BUF_TAUT: lambda s: (s.N,), BUF_LSTORE: lambda s: (2, s.N, s.K),
     }
 
     def get(self, which: int) -> np.ndarray:

@@ -51,8 +51,11 @@ class Steady:
     """R(X; p), J(X; p) and their derivatives on one workload (mesh, DVS, params,
     boundary conditions); the state is passed in, nothing is iterated here."""
 
-    def __init__(self, wl):
+    def __init__(self, wl, L_frozen=None):
+        """L_frozen [2, N, K]: limiter values held fixed (the iteration's frozen
+        limiter); None: the limiter is evaluated at the state."""
         m, d, P = wl.mesh, wl.dvs, wl.params
+        self.L_frozen = None if L_frozen is None else torch.as_tensor(np.asarray(L_frozen), dtype=DT)
         self.wl, self.P = wl, P
         self.N, self.F, self.K = m.n_cell, m.n_face, d.K
         self.u, self.w = _t(d.u), _t(d.w)
@@ -175,6 +178,8 @@ class Steady:
             g = torch.einsum("rs,fks->fkr", self.Minv[i], b)
             if lim == 2:
                 Lm = torch.zeros(2, self.K, dtype=DT)
+            elif lim == 1 and self.L_frozen is not None:
+                Lm = self.L_frozen[:, i, :]
             elif lim == 0:
                 Lm = torch.ones(2, self.K, dtype=DT)
             else:

@@ -44,6 +44,7 @@ struct orc_ctx {
     /* work */
     double *grad, *face0, *face, *fstate, *mface, *microF, *macroF, *Wt, *dW, *taut;
     double *res, *dphi, *rf;
+    double* lstore;                /* [2][N][K] limiter values kept for freezing */
     int prepared;
     int64_t iter;       /* iterations since the last set_state */
 };
@@ -55,6 +56,7 @@ static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1]
 
 #define PHI(buf, fd, i, k) (buf)[((size_t)(fd) * (size_t)c->N + (size_t)(i)) * (size_t)c->K + (size_t)(k)]
 #define FACEV(buf, fd, f, k) (buf)[((size_t)(fd) * (size_t)c->F + (size_t)(f)) * (size_t)c->K + (size_t)(k)]
+#define LSTORE(fd, i, k) c->lstore[((size_t)(fd) * (size_t)c->N + (size_t)(i)) * (size_t)c->K + (size_t)(k)]
 #define GRAD(fd, d, i, k) c->grad[(((size_t)(fd) * 3 + (size_t)(d)) * (size_t)c->N + (size_t)(i)) * (size_t)c->K + (size_t)(k)]
 
 /* VHS viscosity, Eq. T_solve_mu. */
@@ -265,7 +267,7 @@ orc_ctx* orc_create(const orc_params* p) {
 static void free_work(orc_ctx* c) {
     double** bufs[] = {&c->dt, &c->dtimp, &c->eps2, &c->Minv, &c->s, &c->phi, &c->W, &c->q,
                        &c->grad, &c->face0, &c->face, &c->fstate, &c->mface, &c->microF,
-                       &c->macroF, &c->Wt, &c->dW, &c->taut, &c->res, &c->dphi, &c->rf};
+                       &c->macroF, &c->Wt, &c->dW, &c->taut, &c->res, &c->dphi, &c->rf, &c->lstore};
     for (size_t b = 0; b < sizeof(bufs) / sizeof(bufs[0]); ++b) { free(*bufs[b]); *bufs[b] = NULL; }
     free(c->cf_off); free(c->cf_face); free(c->col_off); free(c->col_cell);
     c->cf_off = c->cf_face = c->col_off = c->col_cell = NULL;
@@ -416,6 +418,7 @@ int orc_prepare(orc_ctx* c) {
     c->res = (double*)xcalloc(2 * NK, sizeof(double));
     c->dphi = (double*)xcalloc(2 * NK, sizeof(double));
     c->rf = (double*)xcalloc((size_t)F, sizeof(double));
+    c->lstore = (double*)xcalloc(2 * NK, sizeof(double));
     if (!c->dphi || !c->res || !c->grad || !c->face || !c->face0) return -4;
 
     /* CFL step per cell */
@@ -511,6 +514,13 @@ void orc_step_gradient(orc_ctx* c) {
     /* reading: an optional first-order start (gradient zero) before the limited
      * second-order reconstruction */
     const int lim = (c->iter < c->p.first_order_iters) ? 2 : c->p.limiter;
+    /* reading (no counterpart in the paper): the limiter values may be frozen once
+     * the iteration is close to its fixed point, because the min/max selections of
+     * the limiter otherwise keep switching and stall the residual; iteration
+     * limiter_freeze - 1 stores them, later iterations reuse them */
+    const int freeze = (lim == 1 && c->p.limiter_freeze > 0);
+    const int frozen = freeze && c->iter >= c->p.limiter_freeze;
+    const int store = freeze && c->iter == c->p.limiter_freeze - 1;
     set_implicit_step(c);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
@@ -537,6 +547,8 @@ void orc_step_gradient(orc_ctx* c) {
                 double L = 1.0;
                 if (lim == 2) {
                     L = 0.0;
+                } else if (frozen) {
+                    L = LSTORE(fd, i, k);
                 } else if (lim == 1) {
                     /* limiter at each face centroid, minimum over faces; readings: capped
                      * at 1 so that it only ever reduces the gradient, and the threshold
@@ -552,6 +564,7 @@ void orc_step_gradient(orc_ctx* c) {
                         double psi = orc_venkat(d2 > 0.0 ? dmax : dmin, d2, c->eps2[i] * phii * phii);
                         if (psi < L) L = psi;
                     }
+                    if (store) LSTORE(fd, i, k) = L;
                 }
                 for (int r = 0; r < 3; ++r) GRAD(fd, r, i, k) = L * g[r];
             }
@@ -980,6 +993,7 @@ static double* buffer_ptr(const orc_ctx* c, int which, int64_t* len) {
         case ORC_BUF_DPHI: *len = 2 * NK; return c->dphi;
         case ORC_BUF_S: *len = c->F; return c->s;
         case ORC_BUF_TAUT: *len = c->N; return c->taut;
+        case ORC_BUF_LSTORE: *len = 2 * NK; return c->lstore;
         default: *len = 0; return NULL;
     }
 }

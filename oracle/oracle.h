@@ -40,6 +40,8 @@ typedef struct {
     int32_t n_macro_sgs;   /* PR-SGS iterations of the macro system (40, Sec. 3.2) */
     int32_t limiter;       /* 0 unlimited, 1 Venkatakrishnan, 2 first order        */
     int32_t first_order_iters; /* iterations run first order after set_state      */
+    int32_t limiter_freeze;    /* > 0: from this iteration on the limiter values of
+                                  iteration limiter_freeze - 1 are reused (0: never) */
 } orc_params;
 
 enum { ORC_WALL = 0, ORC_FARFIELD = 1 };
@@ -98,7 +100,8 @@ enum {
     ORC_BUF_DPHI = 11,    /* Delta phi [2][N][K]                                */
     ORC_BUF_DT = 12,      /* [N][3]: CFL step, implicit step, eps^2             */
     ORC_BUF_S = 13,       /* [F] local physical step s_ij                       */
-    ORC_BUF_TAUT = 14     /* [N] predicted relaxation time tau~                  */
+    ORC_BUF_TAUT = 14,    /* [N] predicted relaxation time tau~                  */
+    ORC_BUF_LSTORE = 15   /* [2][N][K] frozen limiter values                      */
 };
 int64_t  orc_buffer_len(const orc_ctx* c, int which);
 int      orc_get(const orc_ctx* c, int which, double* out);

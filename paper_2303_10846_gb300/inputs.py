@@ -109,6 +109,7 @@ class Params:
     n_macro_sgs: int = 40
     limiter: int = 1          # 0 unlimited, 1 Venkatakrishnan, 2 first order
     first_order_iters: int = 0
+    limiter_freeze: int = 0   # > 0: limiter values of iteration limiter_freeze - 1 reused
 
     def as_dict(self):
         return asdict(self)

@@ -162,3 +162,27 @@ def test_adjoint_total_derivative_matches_finite_differences(converged_lid_farfi
         _, rp = st.vjp(x, lam)
         dJdp = (jp + rp).numpy()
         assert np.max(np.abs(fd[:, col] - dJdp)) <= 1e-7 * np.max(np.abs(dJdp)), (which, fd[:, col], dJdp)
+
+
+def test_frozen_limiter_operator():
+    """Limiter freezing: iterations before the freeze are unchanged; afterwards the C
+    oracle reconstructs with the stored limiter values, which the restated operator
+    reproduces when given them (and the stored values are in [0, 1])."""
+    def make(frz):
+        wl = tiny_tet(n_gh=4)
+        wl.params = dataclasses.replace(wl.params, first_order_iters=0, limiter_freeze=frz)
+        return wl
+    o1, o2 = O.Oracle(make(12)), O.Oracle(make(0))
+    o1.iterate(11); o2.iterate(11)
+    assert np.array_equal(o1.get(O.BUF_PHI), o2.get(O.BUF_PHI))
+    o1.iterate(20)
+    L = o1.get(O.BUF_LSTORE)
+    assert L.min() >= 0.0 and L.max() <= 1.0 and L.min() < 1.0
+    phi = torch.as_tensor(o1.get(O.BUF_PHI))
+    o1.step("gradient"); o1.step("faces"); o1.step("fluxes")
+    Fc = o1.get(O.BUF_MICRO_F)
+    wl = make(12)
+    Ff, _ = Steady(wl, L_frozen=L).micro_flux(phi, Steady(wl).p0())
+    Fl, _ = Steady(wl).micro_flux(phi, Steady(wl).p0())
+    assert np.max(np.abs(Ff.numpy() - Fc)) <= 1e-12 * np.max(np.abs(Fc))
+    assert np.max(np.abs(Fl.numpy() - Fc)) > 1e-9 * np.max(np.abs(Fc))
