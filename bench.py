@@ -266,6 +266,34 @@ def run_gpu(args, rank, world, local_rank):
            "h2d_bytes_per_step": int(prim.numel() * 8 / done2),
            "d2h_bytes_per_step": int(6 * 8 + (Wh.numel() + qh.numel()) * 8 / done2)}
 
+    # adjoint of the steady residual (FP64 arithmetic at the context's state): one
+    # vector-Jacobian product, and a fixed number of GMRES iterations of the adjoint solve
+    adj = None
+    if args.adj_iters > 0:
+        s.bind_adjoint(args.adj_krylov)
+        gen = torch.Generator(device=dev).manual_seed(1)
+        v = torch.randn(s.state_len, dtype=torch.float64, device=dev, generator=gen)
+        s.vjp(v)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a0.record(stream)
+        for _ in range(reps):
+            s.vjp(v)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        vjp_ms = a0.elapsed_time(a1) / reps
+        tk = time.perf_counter()
+        it, rel, J, dJdp = s.adjoint_solve("heat", max_iter=args.adj_iters, tol=0.0)
+        torch.cuda.synchronize()
+        tk = time.perf_counter() - tk
+        adj = {"vjp_ms": round(vjp_ms, 3),
+               "vjp_cell_velocity_per_s": N * K / (vjp_ms * 1e-3),
+               "gmres_krylov_dim": args.adj_krylov, "gmres_iterations": it,
+               "s_per_gmres_iteration": round(tk / max(it, 1), 4),
+               "relative_residual_after": rel, "arithmetic": "f64",
+               "state": f"{args.precision} context after {args.steps} end-to-end iterations"}
+
     out = None
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -331,6 +359,7 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "residual_after": float(np.max(res)),
+            "adjoint": adj,
             "wall_s_timed": wall,
         }
     s.close()
@@ -348,6 +377,9 @@ def main():
     ap.add_argument("--start", type=int, default=START_ITERS)
     ap.add_argument("--converge", type=int, default=600,
                     help="iteration cap of the time-to-residual-1e-6 run (0: skip)")
+    ap.add_argument("--adj-iters", type=int, default=8,
+                    help="GMRES iterations of the timed adjoint solve (0: skip the adjoint)")
+    ap.add_argument("--adj-krylov", type=int, default=4)
     ap.add_argument("--kstride", type=int, default=1,
                     help="keep every S-th velocity (weights x S): the smaller case that "
                          "profiler captures of single kernels run on; not a bench line")

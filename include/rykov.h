@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define RK_VERSION 100
+#define RK_VERSION 101
 
 enum {
     RK_OK = 0,
@@ -72,6 +72,11 @@ typedef struct rk_params {
     int32_t n_macro_sgs;   /* PR-SGS iterations of Eq. implicit_mac_equ_fin (40)  */
     int32_t limiter;       /* 0 unlimited, 1 Venkatakrishnan, 2 first order       */
     int32_t first_order_iters; /* first-order iterations after set_state          */
+    int32_t limiter_freeze;    /* > 0 (and > first_order_iters): iterations from this
+                                  one on reuse the limiter values of iteration
+                                  limiter_freeze - 1 (no counterpart in the paper: the
+                                  limiter's switching otherwise stalls the residual);
+                                  0: never                                        */
 } rk_params;
 
 typedef struct rk_ctx rk_ctx;
@@ -213,6 +218,70 @@ int rk_profile_get(rk_ctx* ctx, double* ms, int64_t* counts);
 int rk_residual_noalloc(const double* W_new, const double* W_old, int64_t n_cell,
                         double* res_out, uintptr_t cuda_stream);
 const char* rk_noalloc_last_error(void);
+
+
+/* ---- adjoint of the steady residual operator (FP64 arithmetic) -------------------
+ * A steady state of the implicit iteration (Sec. 3.5 with a zero micro increment and
+ * a zero macro increment) is a zero of R(X; p), X = (phi, W, q):
+ *   R_phi = (phi*(W, q) - phi)/tau(W) - F(phi; p)            Eq. implicit_mic_final_equ
+ *   R_W   = sum_k w Psi (phi - phi*(W, q)), with rho R((1 - 1/Z) T_rot + T/Z) - rho E_rot
+ *           added in the rho E_rot row                        Eqs. solve_rho - solve_Erot
+ *   R_q   = 1/2 sum_k w c|c|^2 (g - g*) + (a_tr - 1) q_tr,  sum_k w c (h - h*) +
+ *           (a_rot - 1) q_rot, c = u - U(W)                    Eqs. solve_qtr, solve_qrot
+ * with F the micro flux of Eq. implicit_mic_flux (interface distribution of Eq.
+ * flux_solve_phi, limited reconstruction of Eq. flux_solve_phi_phi, the boundary
+ * treatment of the iteration) and the limiter of rk_params (the start-up order switch
+ * does not apply).  Parameters p[RK_NPARAM] = (T_w, rho_inf, U_inf x/y/z, T_inf):
+ * p[0] shifts the temperature of every wall boundary, p[1..5] set the state of every
+ * farfield boundary; derivatives are with respect to these shifts.
+ * Objectives (Eqs. cp, cf, ch): RK_OBJ_HEAT = sum over wall faces of A_f q_w,
+ * q_w = sum_k w (u.n)(|u|^2/2 g_f + h_f); RK_OBJ_DRAG = (sum over wall faces of
+ * A_f sum_k w (u.n) u g_f) . e, e = U_inf/|U_inf| of the first farfield boundary
+ * (the x axis if there is none).
+ *
+ * State vectors ("packed", rk_state_len doubles): phi as [2][N][K] (no K padding),
+ * then W[N][6], then q[N][6].  on_device = 1: the pointers are device pointers of that
+ * size; 0: host pointers.  Every call evaluates at the context's current state.
+ *
+ * The adjoint needs a second caller-owned device workspace of
+ * rk_adjoint_workspace_size(ctx, krylov_dim) bytes (256-byte aligned), bound with
+ * rk_bind_adjoint_workspace after rk_bind_workspace; krylov_dim (1..64) is the
+ * dimension of one GMRES restart cycle.  Rebinding the main workspace unbinds it.
+ * RK_MIXED contexts: everything below is evaluated in FP64 at the context's state
+ * (its FP32 distributions widened to FP64); rk_put_state rounds phi to FP32.
+ *
+ *   rk_steady_residual(ctx, r, on_device): r = R(X; p).
+ *   rk_vjp(ctx, v, out, out_params, on_device): out = (dR/dX)^T v, out_params[6] =
+ *       (dR/dp)^T v (out_params may be NULL).  Reverse mode of the kernels: exact up
+ *       to round-off wherever R is differentiable (the limiter's min/max choices are
+ *       held at the ones taken at X).
+ *   rk_objective(ctx, objective, J, dJdX, dJdp, on_device): J(X; p), its gradient
+ *       with respect to X (packed, may be NULL) and its explicit p-derivative dJdp[6].
+ *   rk_adjoint_solve(ctx, objective, max_iter, tol, iters_done, rel_res, J, dJdp):
+ *       solves (dR/dX)^T lam = -dJ/dX by restarted GMRES, right-preconditioned with
+ *       the transposed point Gauss-Seidel sweeps of the micro PR-SGS operator
+ *       (n_micro_sgs x forward + backward colour sweeps; implicit CFL cfl_imp) on the
+ *       phi block and -1 on the (W, q) block; stops when ||(dR/dX)^T lam + dJ/dX||_2 <=
+ *       tol ||dJ/dX||_2 or after max_iter Krylov iterations, starting from the last
+ *       solution of the same objective at the same state (0 otherwise).  Returns the
+ *       iterations done, the final relative residual (recomputed, not estimated),
+ *       J, and the total derivative dJdp[6] = dJ/dp + lam^T dR/dp.  RK_EDIVERGED if
+ *       the residual becomes non-finite.
+ *   rk_adjoint_get(ctx, lam, on_device): the last adjoint solution (packed). */
+#define RK_NPARAM 6
+enum { RK_OBJ_HEAT = 0, RK_OBJ_DRAG = 1 };
+int rk_state_len(const rk_ctx* ctx, int64_t* n);
+int rk_adjoint_workspace_size(rk_ctx* ctx, int32_t krylov_dim, size_t* bytes);
+int rk_bind_adjoint_workspace(rk_ctx* ctx, int32_t krylov_dim, void* dev_ptr, size_t bytes);
+/* X as a packed state vector, and setting X from one (sets phi, W, q as given) */
+int rk_get_state(rk_ctx* ctx, double* x, int on_device);
+int rk_put_state(rk_ctx* ctx, const double* x, int on_device);
+int rk_steady_residual(rk_ctx* ctx, double* r, int on_device);
+int rk_vjp(rk_ctx* ctx, const double* v, double* out, double* out_params, int on_device);
+int rk_objective(rk_ctx* ctx, int objective, double* J, double* dJdX, double* dJdp, int on_device);
+int rk_adjoint_solve(rk_ctx* ctx, int objective, int32_t max_iter, double tol, int32_t* iters_done,
+                     double* rel_res, double* J, double* dJdp);
+int rk_adjoint_get(rk_ctx* ctx, double* lam, int on_device);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,876 @@
+// Device side of the adjoint of the steady residual operator (FP64).
+//
+// Unknowns X = (phi, W, q) of a steady state of the implicit iteration (Sec. 3.5 with
+// dphi = 0 and a zero macro increment), residual R(X; p) = (R_phi, R_W, R_q):
+//   R_phi = (phi*(W, q) - phi)/tau(W) - F(phi; p)          Eq. implicit_mic_final_equ
+//   R_W   = sum_k w Psi (phi - phi*)  (+ rho R((1-1/Z) T_rot + T/Z) - rho E_rot in
+//           the rotational-energy row)                      Eqs. solve_rho - solve_Erot
+//   R_q   = 1/2 sum_k w c|c|^2 (g - g*) + (a_tr - 1) q_tr,
+//           sum_k w c (h - h*) + (a_rot - 1) q_rot           Eqs. solve_qtr, solve_qrot
+// F is the micro flux of Eq. implicit_mic_flux with the interface distribution of
+// Eq. flux_solve_phi and the limited reconstruction of Eq. flux_solve_phi_phi.
+// Parameters p = (T_w shift of every wall, rho_inf, U_inf[3], T_inf of every farfield).
+//
+// The kernels below apply (dR/dX)^T v and (dR/dp)^T v by hand-written reverse mode of
+// the forward kernels: per cell (collision terms and the compensation rows), per
+// interior face (moments -> interface state -> phi* -> blend), per boundary face
+// (wall density rho_w, farfield Maxwellian), and the gradient / Venkatakrishnan
+// limiter / least-squares gather.  Every scatter of the forward pass becomes a gather
+// in a fixed order, so results are bit-reproducible.
+#pragma once
+
+#include "rykov_dev.cuh"
+
+namespace rk {
+
+constexpr int ADJ_FPAR = 12;     // per boundary face: dR/dp^T v (6), J, force (3), 2 spare
+
+struct AdjBufs {
+    double *f0, *fbar;           // [2][F][Kp] phi(x_f - u s) and its adjoint
+    const double *vphi;          // [2][N][Kp] weights v of R_phi
+    double* ophi;                // [2][N][Kp] output (phi part)
+    const double *vW, *vq;       // [N][6]
+    double *oW, *oq;             // [N][6]
+    double* nbg;                 // [2][4][N][Kp] gradient adjoint (3) and Delta adjoint per cell
+    signed char* nbs;            // [2][N][Kp] local slot of the neighbour giving Delta_max/min
+    const int* slot_mirg;        // [nnz] global slot of the same face in the neighbour's list (-1)
+    const double* slot_AVn;      // [nnz] A_f / V_neighbour (0 at boundary faces)
+    const double* tau;           // [N] tau(W_i)
+    double* fpar;                // [Fb][ADJ_FPAR]
+    const double* iterp;         // [4]: [1] reconstruction mode of the steady operator (0-3)
+    double obj_scale;            // weight of the objective seed at wall faces (0: none)
+    int objective;               // 0: heat to the wall, 1: drag
+    double edrag[3];             // drag direction
+};
+
+// ------------------------------------------------------------------------------------
+// reverse mode of one Rykov equilibrium point (Eqs. eqdf_G* - eqdf_Rrot)
+// ------------------------------------------------------------------------------------
+// State in the variables of the formula: theta = R T, theta_tr = R T_tr,
+// theta_rot = R T_rot.  With p = rho theta etc. the equilibrium reads
+//   G^tr = M_tr (1 + (c.q_tr) A_tr),   A_tr = (|c|^2/theta_tr - 5) / (15 rho theta_tr^2)
+//   G^rot = M (1 + w0 (c.q_tr) A),  A = (|c|^2/theta - 5) / (15 rho theta^2)
+//   R^tr = theta_rot G^tr + (1 - delta)(c.q_rot) M_tr / (rho theta_tr)
+//   R^rot = theta G^rot + w1 (1 - delta)(c.q_rot) M / (rho theta)
+// (the same functions as the forward formula, with p_rot theta_tr / theta_rot = rho
+// theta_tr simplified), G* = (1-1/Z) G^tr + G^rot/Z, R* likewise.
+struct EqS {
+    double rho, U[3], th, thtr, throt, qtr[3], qrot[3];
+};
+
+// xb[0] rho, [1-3] U, [4] theta, [5] theta_tr, [6] theta_rot, [7-9] q_tr, [10-12] q_rot
+// += Gb dG*/dx + Hb dR*/dx at velocity u
+__device__ __forceinline__ void eq_vjp(const EqS& s, double om0, double om1, double del, double Z,
+                                       double ux, double uy, double uz, double Gb, double Hb,
+                                       double* xb) {
+    const double c[3] = {ux - s.U[0], uy - s.U[1], uz - s.U[2]};
+    const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    const double cqt = c[0] * s.qtr[0] + c[1] * s.qtr[1] + c[2] * s.qtr[2];
+    const double cqr = c[0] * s.qrot[0] + c[1] * s.qrot[1] + c[2] * s.qrot[2];
+    const double irho = 1.0 / s.rho, itr = 1.0 / s.thtr, it = 1.0 / s.th;
+    const double atr = 2.0 * PI * s.thtr, ar = 2.0 * PI * s.th;
+    const double Mtr = s.rho / (atr * sqrt(atr)) * exp(-0.5 * c2 * itr);
+    const double M = s.rho / (ar * sqrt(ar)) * exp(-0.5 * c2 * it);
+    const double i15r = 1.0 / (15.0 * s.rho);
+    const double Atr = (c2 * itr - 5.0) * itr * itr * i15r;
+    const double Ar = (c2 * it - 5.0) * it * it * i15r;
+    const double Ptr = 1.0 + cqt * Atr;
+    const double Pr = 1.0 + om0 * cqt * Ar;
+    const double Gtr = Mtr * Ptr, Grot = M * Pr;
+    const double Btr = (1.0 - del) * irho * itr;
+    const double Br = om1 * (1.0 - del) * irho * it;
+    const double a1 = 1.0 - 1.0 / Z, a2 = 1.0 / Z;
+    const double htb = a1 * Hb, hrb = a2 * Hb;
+    const double gtb = a1 * Gb + htb * s.throt;
+    const double grb = a2 * Gb + hrb * s.th;
+    double rb = 0.0, thb = 0.0, thtrb = 0.0, Ub[3] = {0.0, 0.0, 0.0}, qtb[3] = {0.0, 0.0, 0.0},
+           qrb[3] = {0.0, 0.0, 0.0}, Mtrb = 0.0, Mb = 0.0;
+    xb[6] += htb * Gtr;
+    thb += hrb * Grot;
+    {   // (1 - delta) (c.q_rot) M_tr / (rho theta_tr)
+        const double X = Btr * cqr * Mtr;
+        const double cqb = htb * Btr * Mtr;
+        Mtrb += htb * Btr * cqr;
+        rb -= htb * X * irho;
+        thtrb -= htb * X * itr;
+        for (int d = 0; d < 3; ++d) { qrb[d] += cqb * c[d]; Ub[d] -= cqb * s.qrot[d]; }
+    }
+    {   // w1 (1 - delta) (c.q_rot) M / (rho theta)
+        const double X = Br * cqr * M;
+        const double cqb = hrb * Br * M;
+        Mb += hrb * Br * cqr;
+        rb -= hrb * X * irho;
+        thb -= hrb * X * it;
+        for (int d = 0; d < 3; ++d) { qrb[d] += cqb * c[d]; Ub[d] -= cqb * s.qrot[d]; }
+    }
+    {   // G^tr = M_tr (1 + (c.q_tr) A_tr)
+        Mtrb += gtb * Ptr;
+        const double Pb = gtb * Mtr;
+        const double cqb = Pb * Atr, Ab = Pb * cqt;
+        const double c2b = Ab * itr * itr * itr * i15r;
+        rb -= Ab * Atr * irho;
+        thtrb += Ab * (10.0 - 3.0 * c2 * itr) * itr * itr * itr * i15r;
+        for (int d = 0; d < 3; ++d) { qtb[d] += cqb * c[d]; Ub[d] -= cqb * s.qtr[d] + 2.0 * c2b * c[d]; }
+    }
+    {   // G^rot = M (1 + w0 (c.q_tr) A)
+        Mb += grb * Pr;
+        const double Pb = grb * M;
+        const double cqb = Pb * om0 * Ar, Ab = Pb * om0 * cqt;
+        const double c2b = Ab * it * it * it * i15r;
+        rb -= Ab * Ar * irho;
+        thb += Ab * (10.0 - 3.0 * c2 * it) * it * it * it * i15r;
+        for (int d = 0; d < 3; ++d) { qtb[d] += cqb * c[d]; Ub[d] -= cqb * s.qtr[d] + 2.0 * c2b * c[d]; }
+    }
+    // Maxwellians rho (2 pi theta)^-3/2 exp(-|c|^2 / (2 theta))
+    rb += Mtrb * Mtr * irho + Mb * M * irho;
+    thtrb += Mtrb * Mtr * (0.5 * c2 * itr * itr - 1.5 * itr);
+    thb += Mb * M * (0.5 * c2 * it * it - 1.5 * it);
+    for (int d = 0; d < 3; ++d) Ub[d] += (Mtrb * Mtr * itr + Mb * M * it) * c[d];
+    xb[0] += rb;
+    for (int d = 0; d < 3; ++d) { xb[1 + d] += Ub[d]; xb[7 + d] += qtb[d]; xb[10 + d] += qrb[d]; }
+    xb[4] += thb;
+    xb[5] += thtrb;
+}
+
+// ------------------------------------------------------------------------------------
+// cell terms: collision part of R_phi and the compensation rows R_W, R_q.
+// mode bit 0: write ophi = the cell part of (dR/dphi)^T v (the face gathers add the
+// flux part later); bit 1: write oW, oq.  One warp per cell.
+// ------------------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a, int mode) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (i >= c.N) return;
+    const double R = c.R, Z = c.Z;
+    const double* W = c.W + 6 * (size_t)i;
+    const double* q = c.q + 6 * (size_t)i;
+    const Prim p = prim_from_W(W, R);
+    const double tau = relax_time(c, p.rho, p.Ttr);
+    const double itau = 1.0 / tau;
+    double e[EQN];
+    make_eq<double, double>(c, p.rho, p.U, p.T, p.Ttr, p.Trot, q, q + 3, e);
+    const EqS st{p.rho, {p.U[0], p.U[1], p.U[2]}, R * p.T, R * p.Ttr, R * p.Trot,
+                 {q[0], q[1], q[2]}, {q[3], q[4], q[5]}};
+    double vW[6], vq[6];
+    for (int d = 0; d < 6; ++d) { vW[d] = a.vW[6 * (size_t)i + d]; vq[d] = a.vq[6 * (size_t)i + d]; }
+    const size_t NK = (size_t)c.N * c.Kp;
+    double acc[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) acc[j] = 0.0;
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+        double G, H;
+        eval_eq(e, ux, uy, uz, G, H);
+        const size_t o = (size_t)i * c.Kp + k;
+        const double g = c.phi[o], h = c.phi[NK + o];
+        const double vg = a.vphi[o], vh = a.vphi[NK + o];
+        const double cx = ux - p.U[0], cy = uy - p.U[1], cz = uz - p.U[2];
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        const double cvt = cx * vq[0] + cy * vq[1] + cz * vq[2];
+        const double cvr = cx * vq[3] + cy * vq[4] + cz * vq[5];
+        const double u2h = 0.5 * (ux * ux + uy * uy + uz * uz);
+        // weights of phi in the compensation rows (moments Psi and the heat fluxes)
+        const double mg = w * (vW[0] + ux * vW[1] + uy * vW[2] + uz * vW[3] + u2h * vW[4] + 0.5 * c2 * cvt);
+        const double mh = w * (vW[4] + vW[5] + cvr);
+        if (mode & 1) {
+            a.ophi[o] = -vg * itau + mg;
+            a.ophi[NK + o] = -vh * itau + mh;
+        }
+        if (mode & 2) {
+            acc[13] -= (vg * (G - g) + vh * (H - h)) * itau * itau;
+            const double dg = g - G, dh = h - H;
+            const double t1 = -0.5 * w * dg, t2 = -w * dh;
+            acc[14] += t1 * (vq[0] * c2 + 2.0 * cx * cvt) + t2 * vq[3];
+            acc[15] += t1 * (vq[1] * c2 + 2.0 * cy * cvt) + t2 * vq[4];
+            acc[16] += t1 * (vq[2] * c2 + 2.0 * cz * cvt) + t2 * vq[5];
+            eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, vg * itau - mg, vh * itau - mh, acc);
+        }
+    }
+    if (!(mode & 2)) return;
+    warp_sum<17>(acc);
+    if (lane != 0) return;
+    double rb = acc[0], Ub[3] = {acc[1] + acc[14], acc[2] + acc[15], acc[3] + acc[16]};
+    double Tb = R * acc[4], Ttrb = R * acc[5], Trotb = R * acc[6], taub = acc[13];
+    double qb[6];
+    for (int d = 0; d < 6; ++d) qb[d] = acc[7 + d];
+    double Wb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, -vW[5]};
+    // rotational-energy row: + rho R ((1 - 1/Z) T_rot + T/Z) - rho E_rot
+    rb += vW[5] * R * ((1.0 - 1.0 / Z) * p.Trot + p.T / Z);
+    Trotb += vW[5] * p.rho * R * (1.0 - 1.0 / Z);
+    Tb += vW[5] * p.rho * R / Z;
+    // heat-flux rows: + (a - 1) q
+    const double atr = (1.0 / 3.0) * (1.0 - (1.0 - c.omega0) / Z);
+    const double arot = (1.0 - c.delta) * (1.0 - (1.0 - c.omega1) / Z);
+    for (int d = 0; d < 3; ++d) { qb[d] += vq[d] * (atr - 1.0); qb[3 + d] += vq[3 + d] * (arot - 1.0); }
+    // tau = mu(T_tr) / (rho R T_tr), mu ~ T_tr^omega
+    Ttrb += taub * tau * (c.omega_vis - 1.0) / p.Ttr;
+    rb -= taub * tau / p.rho;
+    // primitives from W
+    const double k15 = 1.0 / (1.5 * p.rho * R), k25 = 1.0 / (2.5 * p.rho * R), kr = 1.0 / (p.rho * R);
+    double keb = 0.0;
+    Wb[4] += Ttrb * k15; keb -= Ttrb * k15; Wb[5] -= Ttrb * k15; rb -= Ttrb * p.Ttr / p.rho;
+    Wb[5] += Trotb * kr; rb -= Trotb * p.Trot / p.rho;
+    Wb[4] += Tb * k25; keb -= Tb * k25; rb -= Tb * p.T / p.rho;
+    const double U2 = p.U[0] * p.U[0] + p.U[1] * p.U[1] + p.U[2] * p.U[2];
+    rb += keb * 0.5 * U2;
+    double UbU = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        Ub[d] += keb * p.rho * p.U[d];
+        Wb[1 + d] += Ub[d] / p.rho;
+        UbU += Ub[d] * p.U[d];
+    }
+    rb -= UbU / p.rho;
+    Wb[0] += rb;
+    for (int d = 0; d < 6; ++d) { a.oW[6 * (size_t)i + d] = Wb[d]; a.oq[6 * (size_t)i + d] = qb[d]; }
+}
+
+// ------------------------------------------------------------------------------------
+// steady residual R(X; p) from the face distributions phi_ij in c.face (forward face
+// kernels run first): R_phi into a.ophi, R_W into a.oW, R_q into a.oq.  One warp per cell.
+// ------------------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_adj_residual(Dev<double> c, AdjBufs a) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (i >= c.N) return;
+    const double R = c.R, Z = c.Z;
+    const double* W = c.W + 6 * (size_t)i;
+    const double* q = c.q + 6 * (size_t)i;
+    const Prim p = prim_from_W(W, R);
+    const double itau = 1.0 / relax_time(c, p.rho, p.Ttr);
+    double e[EQN];
+    make_eq<double, double>(c, p.rho, p.U, p.T, p.Ttr, p.Trot, q, q + 3, e);
+    const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
+    const int s0 = c.slot_off[i], s1 = c.slot_off[i + 1];
+    double S[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) S[j] = 0.0;
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+        double Fg = 0.0, Fh = 0.0;
+        for (int m = s0; m < s1; ++m) {
+            const int f = c.slot_face[m];
+            double un = dot_rn(ux, uy, uz, c.fn[f], c.fn[c.F + f], c.fn[2 * c.F + f]);
+            if (!c.slot_left[m]) un = -un;
+            Fg += c.slot_AV[m] * un * c.face[(size_t)f * c.Kp + k];
+            Fh += c.slot_AV[m] * un * c.face[FK + (size_t)f * c.Kp + k];
+        }
+        double G, H;
+        eval_eq(e, ux, uy, uz, G, H);
+        const size_t o = (size_t)i * c.Kp + k;
+        const double g = c.phi[o], h = c.phi[NK + o];
+        a.ophi[o] = (G - g) * itau - Fg;
+        a.ophi[NK + o] = (H - h) * itau - Fh;
+        const double dg = g - G, dh = h - H;
+        const double cx = ux - p.U[0], cy = uy - p.U[1], cz = uz - p.U[2];
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        S[0] += w * dg;
+        S[1] += w * ux * dg; S[2] += w * uy * dg; S[3] += w * uz * dg;
+        S[4] += w * (0.5 * (ux * ux + uy * uy + uz * uz) * dg + dh);
+        S[5] += w * dh;
+        S[6] += w * cx * c2 * dg; S[7] += w * cy * c2 * dg; S[8] += w * cz * c2 * dg;
+        S[9] += w * cx * dh; S[10] += w * cy * dh; S[11] += w * cz * dh;
+    }
+    warp_sum<12>(S);
+    if (lane != 0) return;
+    double* oW = a.oW + 6 * (size_t)i;
+    double* oq = a.oq + 6 * (size_t)i;
+    for (int d = 0; d < 5; ++d) oW[d] = S[d];
+    oW[5] = S[5] + p.rho * R * ((1.0 - 1.0 / Z) * p.Trot + p.T / Z) - W[5];
+    const double atr = (1.0 / 3.0) * (1.0 - (1.0 - c.omega0) / Z);
+    const double arot = (1.0 - c.delta) * (1.0 - (1.0 - c.omega1) / Z);
+    for (int d = 0; d < 3; ++d) {
+        oq[d] = 0.5 * S[6 + d] + (atr - 1.0) * q[d];
+        oq[3 + d] = S[9 + d] + (arot - 1.0) * q[3 + d];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// interior faces: reverse of Step 2 (b)-(d).  One warp per face.
+//   pass 1, 2 : moments of phi0 = phi(x_f - u s) (rho, rho U, rho E, sum w h, then the
+//               heat-flux sums and second moments about the interface velocity U)
+//   state     : tau, rho E_rot, T_rot, T_tr, q_tr, q_rot as in the forward kernel
+//   pass A    : adjoint of phi_ij, wb = -A (u.n)(v_L/V_L - v_R/V_R); reductions of
+//               the blend's tau derivative and of phi*'s state derivatives
+//   scalar    : reverse of the interface state down to the moments
+//   pass B    : adjoint of phi0, written to fbar
+// ------------------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, AdjBufs a) {
+    const int lane = threadIdx.x & 31;
+    const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (fi >= c.Fi) return;
+    const int f = c.face_int[fi];
+    const int cl = c.fc[2 * f], cr = c.fc[2 * f + 1];
+    const size_t FK = (size_t)c.F * c.Kp, NK = (size_t)c.N * c.Kp;
+    const double* g0 = a.f0 + (size_t)f * c.Kp;
+    const double* h0 = a.f0 + FK + (size_t)f * c.Kp;
+    const double Rg = c.R, Z = c.Z, s = c.fs[f];
+    double m6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+        const double wg = w * g0[k], wh = w * h0[k];
+        m6[0] += wg;
+        m6[1] += wg * ux; m6[2] += wg * uy; m6[3] += wg * uz;
+        m6[4] += 0.5 * (ux * ux + uy * uy + uz * uz) * wg + wh;
+        m6[5] += wh;
+    }
+    warp_sum<6>(m6);
+    const double rho = m6[0], E = m6[4], Er0 = m6[5];
+    const double U[3] = {m6[1] / rho, m6[2] / rho, m6[3] / rho};
+    const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+    const double ke = 0.5 * rho * U2;
+    const double T = (E - ke) / (2.5 * rho * Rg);
+    const double Ttr0 = (E - ke - Er0) / (1.5 * rho * Rg);
+    const double tau = relax_time(c, rho, Ttr0);
+    const double den = Z * tau + s;
+    const double Erot = (Z * tau * Er0 + s * rho * Rg * T) / den;
+    const double Trot = Erot / (rho * Rg);
+    const double Ttr = (E - ke - Erot) / (1.5 * rho * Rg);
+    double m12[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) m12[j] = 0.0;
+    for (int k = lane; k < c.K; k += 32) {
+        const double cx = c.u[k] - U[0], cy = c.u[c.Kp + k] - U[1], cz = c.u[2 * c.Kp + k] - U[2];
+        const double w = c.w[k];
+        const double wg = w * g0[k], wh = w * h0[k];
+        const double wgc2 = wg * (cx * cx + cy * cy + cz * cz);
+        m12[0] += wgc2 * cx; m12[1] += wgc2 * cy; m12[2] += wgc2 * cz;
+        m12[3] += wh * cx; m12[4] += wh * cy; m12[5] += wh * cz;
+        m12[6] += wg * cx * cx; m12[7] += wg * cy * cy; m12[8] += wg * cz * cz;
+        m12[9] += wg * cx * cy; m12[10] += wg * cx * cz; m12[11] += wg * cy * cz;
+    }
+    warp_sum<12>(m12);
+    const double dtr = tau + s - s / 3.0 * (1.0 - 1.0 / Z + c.omega0 / Z);
+    const double drot = tau + s - s * (1.0 - c.delta) * (1.0 - 1.0 / Z + c.omega1 / Z);
+    double qtr[3], qrot[3];
+    for (int d = 0; d < 3; ++d) {
+        qtr[d] = tau * 0.5 * m12[d] / dtr;
+        qrot[d] = tau * m12[3 + d] / drot;
+    }
+    double e[EQN];
+    make_eq<double, double>(c, rho, U, T, Ttr, Trot, qtr, qrot, e);
+    const EqS st{rho, {U[0], U[1], U[2]}, Rg * T, Rg * Ttr, Rg * Trot,
+                 {qtr[0], qtr[1], qtr[2]}, {qrot[0], qrot[1], qrot[2]}};
+    const double ab = tau / (tau + s), bb = s / (tau + s), db = s / ((tau + s) * (tau + s));
+    const double nx = c.fn[f], ny = c.fn[c.F + f], nz = c.fn[2 * c.F + f], A = c.fa[f];
+    const double iVl = 1.0 / c.vol[cl], iVr = 1.0 / c.vol[cr];
+    const double* vgl = a.vphi + (size_t)cl * c.Kp;
+    const double* vgr = a.vphi + (size_t)cr * c.Kp;
+    double acc[14];
+#pragma unroll
+    for (int j = 0; j < 14; ++j) acc[j] = 0.0;
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k];
+        const double wn = -A * dot_rn(ux, uy, uz, nx, ny, nz);
+        const double wgb = wn * (vgl[k] * iVl - vgr[k] * iVr);
+        const double whb = wn * (vgl[NK + k] * iVl - vgr[NK + k] * iVr);
+        double G, H;
+        eval_eq(e, ux, uy, uz, G, H);
+        acc[13] += (wgb * (g0[k] - G) + whb * (h0[k] - H)) * db;
+        eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, bb * wgb, bb * whb, acc);
+    }
+    warp_sum<14>(acc);
+    // reverse of the interface state
+    double rb = acc[0], Ub[3] = {acc[1], acc[2], acc[3]};
+    double Tb = Rg * acc[4], Ttrb = Rg * acc[5], Trotb = Rg * acc[6], taub = acc[13];
+    double Qtb[3], Qrb[3];
+    for (int d = 0; d < 3; ++d) {
+        Qtb[d] = acc[7 + d] * tau * 0.5 / dtr;
+        taub += acc[7 + d] * 0.5 * m12[d] * (dtr - tau) / (dtr * dtr);
+        Qrb[d] = acc[10 + d] * tau / drot;
+        taub += acc[10 + d] * m12[3 + d] * (drot - tau) / (drot * drot);
+    }
+    {   // heat-flux sums depend on U through c = u - U
+        const double P2 = m12[6] + m12[7] + m12[8];
+        const double S[3][3] = {{m12[6], m12[9], m12[10]}, {m12[9], m12[7], m12[11]}, {m12[10], m12[11], m12[8]}};
+        for (int e2 = 0; e2 < 3; ++e2) {
+            double t = Qtb[e2] * P2 + Qrb[e2] * Er0;
+            for (int d = 0; d < 3; ++d) t += 2.0 * Qtb[d] * S[d][e2];
+            Ub[e2] -= t;
+        }
+    }
+    const double k15 = 1.0 / (1.5 * rho * Rg), k25 = 1.0 / (2.5 * rho * Rg);
+    double Eb = Ttrb * k15, keb = -Ttrb * k15, Erotb = -Ttrb * k15;
+    rb -= Ttrb * Ttr / rho;
+    Erotb += Trotb / (rho * Rg);
+    rb -= Trotb * Trot / rho;
+    taub += Erotb * Z * (Er0 - Erot) / den;
+    double Er0b = Erotb * Z * tau / den;
+    rb += Erotb * s * Rg * T / den;
+    Tb += Erotb * s * rho * Rg / den;
+    const double Ttr0b = taub * tau * (c.omega_vis - 1.0) / Ttr0;
+    rb -= taub * tau / rho;
+    Eb += Ttr0b * k15; keb -= Ttr0b * k15; Er0b -= Ttr0b * k15;
+    rb -= Ttr0b * Ttr0 / rho;
+    Eb += Tb * k25; keb -= Tb * k25;
+    rb -= Tb * T / rho;
+    rb += keb * 0.5 * U2;
+    double mb[3], UbU = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        Ub[d] += keb * rho * U[d];
+        mb[d] = Ub[d] / rho;
+        UbU += Ub[d] * U[d];
+    }
+    rb -= UbU / rho;
+    double* gb = a.fbar + (size_t)f * c.Kp;
+    double* hb = a.fbar + FK + (size_t)f * c.Kp;
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+        const double wn = -A * dot_rn(ux, uy, uz, nx, ny, nz);
+        const double wgb = wn * (vgl[k] * iVl - vgr[k] * iVr);
+        const double whb = wn * (vgl[NK + k] * iVl - vgr[NK + k] * iVr);
+        const double cx = ux - U[0], cy = uy - U[1], cz = uz - U[2];
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        gb[k] = ab * wgb + w * (rb + mb[0] * ux + mb[1] * uy + mb[2] * uz +
+                                Eb * 0.5 * (ux * ux + uy * uy + uz * uz) +
+                                c2 * (Qtb[0] * cx + Qtb[1] * cy + Qtb[2] * cz));
+        hb[k] = ab * whb + w * (Eb + Er0b + Qrb[0] * cx + Qrb[1] * cy + Qrb[2] * cz);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// boundary faces: reverse of the wall / farfield treatment (no interface collision).
+// Seeds: -A (u.n) v_i / V_i from R_phi, plus obj_scale times the derivative of the
+// objective at wall faces (heat: A w (u.n)(|u|^2/2 g + h); drag: A w (u.n)(u.e) g).
+// Writes fbar at outgoing velocities and per face fpar = (dT_w, drho_inf, dU_inf[3],
+// dT_inf, J_f, force_f[3]).  One block per boundary face.
+// ------------------------------------------------------------------------------------
+template <int BS>
+__global__ void __launch_bounds__(BS) k_adj_face_boundary(Dev<double> c, AdjBufs a) {
+    __shared__ double red[12 * (BS / 32)];
+    __shared__ double sh[4];
+    const int b = blockIdx.x;
+    const int f = c.face_bnd[b];
+    const int bc = -1 - c.fc[2 * f + 1];
+    const int kind = c.bck[bc];
+    const int i = c.fc[2 * f];
+    const size_t FK = (size_t)c.F * c.Kp, NK = (size_t)c.N * c.Kp;
+    const double* g0 = a.f0 + (size_t)f * c.Kp;
+    const double* h0 = a.f0 + FK + (size_t)f * c.Kp;
+    double* gbar = a.fbar + (size_t)f * c.Kp;
+    double* hbar = a.fbar + FK + (size_t)f * c.Kp;
+    const double nx = c.fn[f], ny = c.fn[c.F + f], nz = c.fn[2 * c.F + f], A = c.fa[f];
+    const double iV = 1.0 / c.vol[i];
+    const double* bv = c.bcv + 5 * bc;
+    const double Tb0 = bv[4], RT = c.R * Tb0;
+    const double rho_b = (kind == 0) ? 1.0 : bv[0];
+    const double an = 2.0 * PI * RT;
+    const double Mn = rho_b / (an * sqrt(an)), Mx = 1.0 / (2.0 * RT);
+    const bool wall = kind == 0;
+    const double seed = wall ? a.obj_scale : 0.0;
+    const double* vg = a.vphi + (size_t)i * c.Kp;
+    double num = 0.0, dn = 0.0;
+    if (wall) {
+        double v[2] = {0.0, 0.0};
+        for (int k = threadIdx.x; k < c.K; k += BS) {
+            const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+            const double un = dot_rn(ux, uy, uz, nx, ny, nz);
+            if (un > 0.0) {
+                v[0] += w * un * g0[k];
+            } else {
+                const double cx = ux - bv[1], cy = uy - bv[2], cz = uz - bv[3];
+                v[1] += -w * un * Mn * exp(-(cx * cx + cy * cy + cz * cz) * Mx);
+            }
+        }
+        block_sum<2, BS>(v, red);
+        num = v[0];
+        dn = v[1];
+    }
+    const double rw = wall ? num / dn : 1.0;
+    double acc[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = 0.0;
+    // acc: 0 rho_w adjoint, 1 T_w adjoint (direct), 2 d(den)/dT_w, 3 rho_inf, 4-6 U_inf,
+    //      7 T_inf, 8 J_f, 9-11 force_f
+    for (int k = threadIdx.x; k < c.K; k += BS) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+        const double un = dot_rn(ux, uy, uz, nx, ny, nz);
+        const double u2h = 0.5 * (ux * ux + uy * uy + uz * uz);
+        double wgb = -A * un * vg[k] * iV, whb = -A * un * vg[NK + k] * iV;
+        if (seed != 0.0) {
+            if (a.objective == 0) {
+                wgb += seed * A * w * un * u2h;
+                whb += seed * A * w * un;
+            } else {
+                wgb += seed * A * w * un * (ux * a.edrag[0] + uy * a.edrag[1] + uz * a.edrag[2]);
+            }
+        }
+        double gf, hf;
+        if (un > 0.0) {
+            gf = g0[k];
+            hf = h0[k];
+            gbar[k] = wgb;
+            hbar[k] = whb;
+        } else {
+            const double cx = ux - bv[1], cy = uy - bv[2], cz = uz - bv[3];
+            const double c2 = cx * cx + cy * cy + cz * cz;
+            const double M = Mn * exp(-c2 * Mx);
+            const double dMdT = M * (c2 / (2.0 * c.R * Tb0 * Tb0) - 1.5 / Tb0);
+            if (wall) {
+                gf = rw * M;
+                hf = RT * gf;
+                acc[0] += wgb * M + whb * RT * M;
+                acc[1] += wgb * rw * dMdT + whb * rw * c.R * (M + Tb0 * dMdT);
+                acc[2] += -w * un * dMdT;
+            } else {
+                gf = M;
+                hf = RT * M;
+                const double X = wgb + whb * RT;
+                acc[3] += X * M / rho_b;
+                acc[4] += X * M * cx / RT;
+                acc[5] += X * M * cy / RT;
+                acc[6] += X * M * cz / RT;
+                acc[7] += X * dMdT + whb * c.R * M;
+            }
+        }
+        if (wall) {
+            acc[8] += A * w * un * (u2h * gf + hf);
+            acc[9] += A * w * un * ux * gf;
+            acc[10] += A * w * un * uy * gf;
+            acc[11] += A * w * un * uz * gf;
+        }
+    }
+    block_sum<12, BS>(acc, red);
+    if (threadIdx.x == 0) {
+        double* o = a.fpar + (size_t)b * ADJ_FPAR;
+        double numb = 0.0;
+        for (int j = 0; j < ADJ_FPAR; ++j) o[j] = 0.0;
+        if (wall) {
+            numb = acc[0] / dn;
+            o[0] = acc[1] - acc[0] * num / (dn * dn) * acc[2];
+            o[6] = a.objective == 0 ? acc[8]
+                                    : acc[9] * a.edrag[0] + acc[10] * a.edrag[1] + acc[11] * a.edrag[2];
+            o[7] = acc[9]; o[8] = acc[10]; o[9] = acc[11];
+        } else {
+            for (int j = 0; j < 5; ++j) o[1 + j] = acc[3 + j];
+        }
+        sh[0] = numb;
+    }
+    __syncthreads();
+    if (wall) {
+        const double numb = sh[0];
+        for (int k = threadIdx.x; k < c.K; k += BS) {
+            const double un = dot_rn(c.u[k], c.u[c.Kp + k], c.u[2 * c.Kp + k], nx, ny, nz);
+            if (un > 0.0) gbar[k] += numb * c.w[k] * un;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// cell gather 1: adjoint of phi0 from the faces where the cell is upwind, then the
+// reverse of phi0 = phi_c + (x_f - u s - x_c) . L g (Eq. flux_solve_phi_phi) through the
+// Venkatakrishnan limiter (Sec. 3.3 readings: minimum over faces capped at 1, eps^2
+// phi_c^2 threshold) and the least-squares gradient g = sum_j M^-1 d_j (phi_j - phi_c).
+// Adds the cell's own terms to ophi and leaves, per (cell, velocity, field), the
+// gradient adjoint and the Delta_max/min adjoint with the slot of the neighbour that
+// gave it, for the neighbours to gather.  One warp per cell.
+// ------------------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs a) {
+    __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_left[WPB][MAXF];
+    __shared__ double s_lsq[WPB][3][MAXF], s_d[WPB][3][MAXF], s_n[WPB][3][MAXF], s_s[WPB][MAXF];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int i = blockIdx.x * WPB + wp;
+    if (i >= c.N) return;
+    const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
+    if (lane < ns) {
+        const int m = s0 + lane;
+        const int f = c.slot_face[m];
+        s_face[wp][lane] = f;
+        s_nbr[wp][lane] = c.slot_nbr[m];
+        s_left[wp][lane] = c.slot_left[m];
+        s_s[wp][lane] = c.fs[f];
+        for (int r = 0; r < 3; ++r) {
+            s_lsq[wp][r][lane] = c.slot_lsq[r * c.nnz + m];
+            s_d[wp][r][lane] = c.slot_d[r * c.nnz + m];
+            s_n[wp][r][lane] = c.slot_n[r * c.nnz + m];
+        }
+    }
+    __syncwarp();
+    const double eps2 = c.eps2[i];
+    const int limiter = (int)a.iterp[1];
+    const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k];
+        for (int fd = 0; fd < 2; ++fd) {
+            const double* ph = c.phi + fd * NK;
+            const double pc = ph[(size_t)i * c.Kp + k];
+            // forward: gradient, Delta_max/min with the slot that gave them
+            double g[3] = {0.0, 0.0, 0.0}, dmax = 0.0, dmin = 0.0;
+            int amax = -1, amin = -1;
+            for (int q = 0; q < ns; ++q) {
+                const int j = s_nbr[wp][q];
+                if (j < 0) continue;
+                const double dp = ph[(size_t)j * c.Kp + k] - pc;
+                g[0] += s_lsq[wp][0][q] * dp; g[1] += s_lsq[wp][1][q] * dp; g[2] += s_lsq[wp][2][q] * dp;
+                if (dp > dmax) { dmax = dp; amax = q; }
+                if (dp < dmin) { dmin = dp; amin = q; }
+            }
+            double L = (limiter == 2) ? 0.0 : 1.0;
+            int lq = -1;
+            if (limiter == 3) {
+                L = c.lstore[fd * NK + (size_t)i * c.Kp + k];     // frozen: a constant
+            } else if (limiter == 1) {
+                double bn = 1.0, bd = 1.0;
+                const double ep = eps2 * pc * pc;
+                for (int q = 0; q < ns; ++q) {
+                    const double d2 = g[0] * s_d[wp][0][q] + g[1] * s_d[wp][1][q] + g[2] * s_d[wp][2][q];
+                    if (d2 == 0.0) continue;
+                    const double d1 = d2 > 0.0 ? dmax : dmin;
+                    const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
+                    const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
+                    if (nu * bd < bn * de) { bn = nu; bd = de; lq = q; }
+                }
+                L = bn / bd;
+            }
+            // adjoint of phi0 gathered over the faces where this cell is upwind
+            double self = 0.0, Gb[3] = {0.0, 0.0, 0.0};
+            const double* fb = a.fbar + fd * FK;
+            for (int q = 0; q < ns; ++q) {
+                const double un = dot_rn(ux, uy, uz, s_n[wp][0][q], s_n[wp][1][q], s_n[wp][2][q]);
+                const bool up = s_left[wp][q] ? (un > 0.0) : (un <= 0.0);
+                if (!up) continue;
+                const double x = fb[(size_t)s_face[wp][q] * c.Kp + k];
+                const double sq = s_s[wp][q];
+                self += x;
+                Gb[0] += (s_d[wp][0][q] - ux * sq) * x;
+                Gb[1] += (s_d[wp][1][q] - uy * sq) * x;
+                Gb[2] += (s_d[wp][2][q] - uz * sq) * x;
+            }
+            // reverse of L g
+            const double Lb = Gb[0] * g[0] + Gb[1] * g[1] + Gb[2] * g[2];
+            double gb[3] = {L * Gb[0], L * Gb[1], L * Gb[2]};
+            double d1b = 0.0;
+            int slot = -1;
+            if (limiter == 1 && lq >= 0) {
+                const double dx = s_d[wp][0][lq], dy = s_d[wp][1][lq], dz = s_d[wp][2][lq];
+                const double d2 = g[0] * dx + g[1] * dy + g[2] * dz;
+                const double d1 = d2 > 0.0 ? dmax : dmin;
+                const double ep = eps2 * pc * pc;
+                const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
+                const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
+                const double ide2 = 1.0 / (de * de);
+                const double pd1 = ((2.0 * d1 + 2.0 * d2) * de - nu * (2.0 * d1 + d2)) * ide2;
+                const double pd2 = (2.0 * d1 * de - nu * (4.0 * d2 + d1)) * ide2;
+                const double pep = (de - nu) * ide2;
+                gb[0] += Lb * pd2 * dx; gb[1] += Lb * pd2 * dy; gb[2] += Lb * pd2 * dz;
+                self += Lb * pep * 2.0 * eps2 * pc;
+                const int arg = d2 > 0.0 ? amax : amin;
+                if (arg >= 0) {
+                    d1b = Lb * pd1;
+                    self -= d1b;
+                    slot = arg;
+                }
+            }
+            // reverse of the least-squares gradient: the cell's own part
+            for (int q = 0; q < ns; ++q) {
+                if (s_nbr[wp][q] < 0) continue;
+                self -= s_lsq[wp][0][q] * gb[0] + s_lsq[wp][1][q] * gb[1] + s_lsq[wp][2][q] * gb[2];
+            }
+            const size_t o = (size_t)i * c.Kp + k;
+            a.ophi[fd * NK + o] += self;
+            double* nb = a.nbg + (size_t)fd * 4 * NK;
+            nb[o] = gb[0];
+            nb[NK + o] = gb[1];
+            nb[2 * NK + o] = gb[2];
+            nb[3 * NK + o] = d1b;
+            a.nbs[fd * NK + o] = (signed char)slot;
+        }
+    }
+}
+
+// cell gather 2: the neighbours' gradient and Delta terms that involve this cell's
+// value: sum over neighbours c of  lsq_c(this) . gb_c  +  [c's Delta came from this
+// cell] d1b_c.  One warp per cell.
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_adj_gather2(Dev<double> c, AdjBufs a) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (i >= c.N) return;
+    const int s0 = c.slot_off[i], s1 = c.slot_off[i + 1];
+    const size_t NK = (size_t)c.N * c.Kp;
+    for (int k = lane; k < c.K; k += 32) {
+        double acc[2] = {0.0, 0.0};
+        for (int m = s0; m < s1; ++m) {
+            const int j = c.slot_nbr[m];
+            if (j < 0) continue;
+            const int mm = a.slot_mirg[m];
+            const int loc = mm - c.slot_off[j];
+            const double lx = c.slot_lsq[mm], ly = c.slot_lsq[c.nnz + mm], lz = c.slot_lsq[2 * c.nnz + mm];
+            const size_t o = (size_t)j * c.Kp + k;
+            for (int fd = 0; fd < 2; ++fd) {
+                const double* nb = a.nbg + (size_t)fd * 4 * NK;
+                double t = lx * nb[o] + ly * nb[NK + o] + lz * nb[2 * NK + o];
+                if (a.nbs[fd * NK + o] == loc) t += nb[3 * NK + o];
+                acc[fd] += t;
+            }
+        }
+        const size_t o = (size_t)i * c.Kp + k;
+        a.ophi[o] += acc[0];
+        a.ophi[NK + o] += acc[1];
+    }
+}
+
+// Sum of the per-boundary-face records in face order (one block of 32 threads): out[0-5]
+// (dR/dp)^T v or dJ/dp|_X, out[6] J, out[7-9] force.
+__global__ void k_adj_params(const double* fpar, int Fb, double* out) {
+    const int j = threadIdx.x;
+    if (j >= 10) return;
+    double s = 0.0;
+    for (int b = 0; b < Fb; ++b) s += fpar[(size_t)b * ADJ_FPAR + j];
+    out[j] = s;
+}
+
+// ------------------------------------------------------------------------------------
+// preconditioner: transposed point Gauss-Seidel sweep of the first-order implicit
+// operator of Eq. implicit_mic_final_equ for the cells of one colour,
+//   y_i = (r_i + sum_j (A/V_j) max(u.n_ij, 0) y_j) / D_i,
+//   D_i = 1/(cfl dt_i) + 1/tau_i + sum_f (A/V_i) max(u.n_if, 0)
+// (the transpose of the micro PR-SGS operator: entry (i, j) is (A/V_j) min(u.n_ji, 0)).
+// One warp per cell.
+// ------------------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_adj_sweep(Dev<double> c, AdjBufs a, const int* cells,
+                                                        int n, const double* r, double* y) {
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (t >= n) return;
+    const int i = cells[t];
+    const int s0 = c.slot_off[i], s1 = c.slot_off[i + 1];
+    const size_t NK = (size_t)c.N * c.Kp;
+    const double base = 1.0 / (c.cfl_imp * c.dt[i]) + 1.0 / a.tau[i];
+    for (int k = lane; k < c.K; k += 32) {
+        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k];
+        double D = base, ag = 0.0, ah = 0.0;
+        for (int m = s0; m < s1; ++m) {
+            double un = dot_rn(ux, uy, uz, c.slot_n[m], c.slot_n[c.nnz + m], c.slot_n[2 * c.nnz + m]);
+            if (!c.slot_left[m]) un = -un;
+            if (!(un > 0.0)) continue;
+            D += c.slot_AV[m] * un;
+            const int j = c.slot_nbr[m];
+            if (j < 0) continue;
+            const double cf = a.slot_AVn[m] * un;
+            ag += cf * y[(size_t)j * c.Kp + k];
+            ah += cf * y[NK + (size_t)j * c.Kp + k];
+        }
+        const size_t o = (size_t)i * c.Kp + k;
+        y[o] = (r[o] + ag) / D;
+        y[NK + o] = (r[NK + o] + ah) / D;
+    }
+}
+
+// tau(W_i) per cell
+__global__ void k_adj_tau(Dev<double> c, double* tau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
+    const Prim p = prim_from_W(c.W + 6 * (size_t)i, c.R);
+    tau[i] = relax_time(c, p.rho, p.Ttr);
+}
+
+// ------------------------------------------------------------------------------------
+// vectors X = (phi [2][N][K], W [N][6], q [N][6]) in the packed (unpadded) layout of the
+// interface <-> padded internal arrays
+// ------------------------------------------------------------------------------------
+__global__ void k_adj_unpack(const double* x, int N, int K, int Kp, double* phi, double* W, double* q) {
+    const size_t n1 = 2 * (size_t)N * K;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t < n1) {
+        const size_t row = t / K, k = t % K;
+        phi[row * Kp + k] = x[t];
+    } else if (t < n1 + 6 * (size_t)N) {
+        W[t - n1] = x[t];
+    } else if (t < n1 + 12 * (size_t)N) {
+        q[t - n1 - 6 * (size_t)N] = x[t];
+    }
+}
+
+__global__ void k_adj_pack(const double* phi, const double* W, const double* q, int N, int K, int Kp, double* x) {
+    const size_t n1 = 2 * (size_t)N * K;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t < n1) {
+        const size_t row = t / K, k = t % K;
+        x[t] = phi[row * Kp + k];
+    } else if (t < n1 + 6 * (size_t)N) {
+        x[t] = W[t - n1];
+    } else if (t < n1 + 12 * (size_t)N) {
+        x[t] = q[t - n1 - 6 * (size_t)N];
+    }
+}
+
+// per-velocity arrays of a mixed-precision context in FP64 and back, and s_ij per slot
+__global__ void k_adj_upcast(const float* src, double* dst, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        dst[t] = (double)src[t];
+}
+__global__ void k_adj_downcast(const double* src, float* dst, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
+}
+__global__ void k_adj_slot_s(DevBase c, double* slot_s) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < c.nnz) slot_s[m] = c.fs[c.slot_face[m]];
+}
+
+// ------------------------------------------------------------------------------------
+// Krylov vector kernels on packed vectors of length n (deterministic: fixed grid, block
+// partial sums combined in block order by k_vec_finish)
+// ------------------------------------------------------------------------------------
+constexpr int VEC_BS = 256, VEC_GRID = 1024;
+constexpr int GM_MAX = 64;      // maximum Krylov dimension of one restart cycle
+
+// part[b * m + j] = sum over the block's range of x . V_j, j < m (V_j = V + j * ld)
+__global__ void __launch_bounds__(VEC_BS) k_vec_mdot(const double* x, const double* V, size_t ld, int m,
+                                                      size_t n, double* part) {
+    __shared__ double red[VEC_BS / 32];
+    for (int j = 0; j < m; ++j) {
+        const double* v = V + (size_t)j * ld;
+        double s = 0.0;
+        for (size_t t = blockIdx.x * (size_t)VEC_BS + threadIdx.x; t < n; t += (size_t)VEC_GRID * VEC_BS)
+            s += x[t] * v[t];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tsum = red[0];
+            for (int q = 1; q < VEC_BS / 32; ++q) tsum += red[q];
+            part[(size_t)blockIdx.x * m + j] = tsum;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_vec_finish(const double* part, int m, double* out) {
+    const int j = threadIdx.x;
+    if (j >= m) return;
+    double s = 0.0;
+    for (int b = 0; b < VEC_GRID; ++b) s += part[(size_t)b * m + j];
+    out[j] = s;
+}
+
+// x -= sum_j h[j] V_j  (h on the device)
+__global__ void k_vec_msub(double* x, const double* V, size_t ld, int m, const double* h, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        double s = x[t];
+        for (int j = 0; j < m; ++j) s -= h[j] * V[(size_t)j * ld + t];
+        x[t] = s;
+    }
+}
+
+// y = a x + b y (a term with a zero coefficient is not read)
+__global__ void k_vec_axpby(double a, const double* x, double b, double* y, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        y[t] = (a == 0.0 ? 0.0 : a * x[t]) + (b == 0.0 ? 0.0 : b * y[t]);
+}
+
+// y += sum_j c[j] V_j  (c on the device)
+__global__ void k_vec_madd(double* y, const double* V, size_t ld, int m, const double* cc, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        double s = y[t];
+        for (int j = 0; j < m; ++j) s += cc[j] * V[(size_t)j * ld + t];
+        y[t] = s;
+    }
+}
+
+}  // namespace rk

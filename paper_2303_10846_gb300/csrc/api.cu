@@ -10,87 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "rykov.h"
-#include "rykov_launch.cuh"
-
-namespace {
-
-constexpr int MAX_BC = 64;
-constexpr int RK_DEBUG_FLAG = 0x100;   // precision flag: reserve verification buffers
-
-struct Carver {
-    char* base;
-    size_t off = 0;
-    template <typename X>
-    X* take(size_t n) {
-        off = (off + 255) & ~size_t(255);
-        X* p = base ? reinterpret_cast<X*>(base + off) : nullptr;
-        off += n * sizeof(X);
-        return p;
-    }
-};
-
-}  // namespace
-
-struct rk_ctx {
-    int prec = RK_FP64;
-    bool debug = false;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    rk_params p{};
-    bool have_params = false;
-    // staged inputs
-    int64_t N = 0, F = 0, K = 0;
-    std::vector<int64_t> fc;
-    std::vector<double> fn, fa, fx, cx, cv;
-    std::vector<int32_t> col;
-    std::vector<double> u, w;
-    int bck[MAX_BC];
-    double bcv[MAX_BC * 5];
-    // derived (host)
-    int Kp = 0, C = 0, nnz = 0, Fi = 0, Fb = 0, nwall = 0;
-    std::vector<int> slot_off, slot_face, slot_nbr, slot_left, slot_ncol, face_int, face_bnd,
-        col_off, col_cell, wall_b, fc32;
-    std::vector<double> slot_n;
-    bool mesh_ok = false, dvs_ok = false;
-    // device
-    char* ws = nullptr;
-    size_t ws_bytes = 0;
-    bool bound = false;
-    rk::Dev<double> dd{};
-    rk::Dev<float> df{};
-    rk::Sched sched{};
-    rk::Prof prof{};
-    double *stage_a = nullptr, *stage_b = nullptr;   // [N][6] staging for host inputs
-    double* surf_out = nullptr;                       // [nwall][8]
-    double* surf_contrib = nullptr;                   // [nwall][4]
-    double* surf_tot = nullptr;                       // [4]
-    int* wall_b_dev = nullptr;
-    void* dbg = nullptr;                              // [2][N][Kp] T (debug contexts)
-    double* pin = nullptr;                            // pinned host: 16 doubles
-    int64_t iter = 0;
-    bool have_state = false;
-    // CUDA graph of one implicit iteration (captured on a private stream, launched on
-    // the caller's stream); rebuilt after anything baked into it changes
-    bool use_graph = true;
-    bool use_coop = false;            // cooperative launch of the macro PR-SGS (RYKOV_COOP=1)
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    long long graph_kernels = 0;
-    double last_res[6] = {0, 0, 0, 0, 0, 0};
-};
-
-static int fail(rk_ctx* c, int code, const std::string& msg) {
-    if (c) c->err = msg;
-    return code;
-}
-
-#define CK(call)                                                                        \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess)                                                          \
-            return fail(ctx, RK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
+#include "rykov_ctx.h"
 
 static double implicit_cfl(const rk_params& p, int64_t n) {
     if (p.cfl_imp0 <= 0.0 || p.cfl_ramp <= 1.0) return p.cfl_imp;
@@ -131,6 +51,7 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
 
 extern "C" int rk_destroy(rk_ctx* ctx) {
     if (!ctx) return RK_EINVAL;
+    rk_adj_release(ctx);
     if (ctx->pin) cudaFreeHost(ctx->pin);
     for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
@@ -145,7 +66,8 @@ extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
     if (!ctx || !p) return RK_EINVAL;
     if (!(p->R > 0) || !(p->Z_rot >= 1.0) || !(p->mu_ref > 0) || !(p->T_ref > 0) ||
         !(p->cfl_s > 0) || !(p->cfl_imp > 0) || p->n_micro_sgs < 1 || p->n_macro_sgs < 0 ||
-        p->limiter < 0 || p->limiter > 2 || !(p->lim_k >= 0))
+        p->limiter < 0 || p->limiter > 2 || !(p->lim_k >= 0) || p->limiter_freeze < 0 ||
+        (p->limiter_freeze > 0 && p->limiter_freeze <= p->first_order_iters))
         return fail(ctx, RK_EINVAL, "rk_set_params: parameter out of range");
     bool geo_change = ctx->p.cfl_s != p->cfl_s || ctx->p.lim_k != p->lim_k;
     ctx->p = *p;
@@ -164,6 +86,7 @@ extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
         d.cfl_s = p->cfl_s; d.lim_k = p->lim_k;
         d.cfl_imp = p->cfl_imp; d.cfl_imp0 = p->cfl_imp0; d.cfl_ramp = p->cfl_ramp;
         d.first_order_iters = p->first_order_iters; d.limiter = p->limiter;
+        d.limiter_freeze = p->limiter_freeze;
         using TT = std::remove_reference_t<decltype(d.tp[0])>;
         const double v[8] = {p->R, p->Z_rot, p->mu_ref, p->T_ref, p->omega_vis, p->omega0, p->omega1, p->delta};
         for (int j = 0; j < 8; ++j) d.tp[j] = (TT)v[j];
@@ -344,6 +267,7 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.u = cv.take<double>(3 * Kp); d.w = cv.take<double>(Kp);
     d.uT = cv.take<T>(3 * Kp); d.wT = cv.take<T>(Kp);
     d.phi = cv.take<T>(2 * N * Kp); d.face = cv.take<T>(2 * F * Kp);
+    d.lstore = cv.take<T>(2 * N * Kp);
     d.res = cv.take<T>(2 * N * Kp); d.dphi = cv.take<T>(2 * N * Kp);
     d.W = cv.take<double>(6 * N); d.q = cv.take<double>(6 * N); d.Wold = cv.take<double>(6 * N);
     d.fstate = cv.take<double>(rk::FST * F); d.mface = cv.take<double>(6 * F);
@@ -456,6 +380,7 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
     CK(cudaStreamSynchronize(s));
     ctx->bound = true;
     ctx->have_state = false;
+    ctx->bind_gen++;
     return RK_OK;
 }
 
@@ -497,6 +422,7 @@ static int set_state_prim_impl(rk_ctx* ctx, rk::Dev<T>& d, const double* prim, c
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->iter = 0;
     ctx->have_state = true;
+    ctx->state_ver++;
     return RK_OK;
 }
 
@@ -532,6 +458,7 @@ extern "C" int rk_set_state(rk_ctx* ctx, const double* W, const double* q, const
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->iter = 0;
     ctx->have_state = true;
+    ctx->state_ver++;
     return RK_OK;
 }
 
@@ -565,6 +492,7 @@ static int step_impl(rk_ctx* ctx, rk::Dev<T>& d, int step) {
     cudaError_t e = launch_step(ctx, d, step, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, RK_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     if (step == RK_STEP_MICRO) ctx->iter++;
+    ctx->state_ver++;
     return RK_OK;
 }
 
@@ -608,6 +536,7 @@ static int iteration(rk_ctx* ctx, rk::Dev<T>& d) {
             CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
             ctx->prof.launches += ctx->graph_kernels;
             ctx->iter++;
+            ctx->state_ver++;
             return RK_OK;
         }
     }

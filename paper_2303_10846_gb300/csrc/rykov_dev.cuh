@@ -22,16 +22,17 @@ constexpr int CEQ = 28;        // per-cell record: EQN constants, 1/tau~, diagon
 constexpr int FST = 16;        // face state record
 constexpr double PI = 3.14159265358979323846;
 
-template <typename T>
-struct Dev {
+// Fields that do not depend on the per-velocity type T (FP64 geometry, per-cell and
+// per-face state, parameters); Dev<T> adds the per-velocity arrays and their T copies.
+struct DevBase {
     int N, F, K, Kp, C, Fi, Fb, nnz;
     int debug;                         // write verification-only records (face states)
-    // R, Z, mu_ref, T_ref, omega_vis, omega0, omega1, delta in T (no conversions in kernels)
-    T tp[8];
     // implicit-step schedule, evaluated on the device each iteration (k_iter_begin)
     double cfl_imp, cfl_imp0, cfl_ramp;
-    int first_order_iters, limiter;
-    double* iterp;                     // [0] cfl, [1] limiter, [2] iteration counter
+    int first_order_iters, limiter, limiter_freeze;
+    // [0] cfl, [1] reconstruction mode (0 unlimited, 1 limited, 2 first order,
+    // 3 limited with the stored limiter values, 4 limited and store them), [2] counter
+    double* iterp;
     // gas / scheme parameters
     double R, Z, omega_vis, mu_ref, T_ref, omega0, omega1, delta, cfl_s, lim_k;
     // cells
@@ -44,20 +45,16 @@ struct Dev {
     double *slot_AV;                   // A_f / V_i  [nnz]
     double *slot_d;                    // x_f - x_i  [3][nnz]
     double *slot_lsq;                  // LSQ weight vector M_i^{-1}(x_j - x_i), 0 at boundaries [3][nnz]
-    T *slot_nT, *slot_AVT, *slot_dT, *slot_lsqT, *slot_sT;
     // faces
     const int* fc;                     // [F][2]
     const double *fn, *fa, *fxc;       // [3][F], [F], [3][F]
     double *fs, *fdl, *rf;             // s_ij, distance used in r_ij, r_ij  [F]
-    T *fnT, *fsT;                      // face normal [3][F] and s_ij [F] in T
     const int *face_int, *face_bnd;    // lists
     const double* bcv;                 // [64][5]: rho, U, T
     const int* bck;                    // [64] kind
     // discrete velocity space (SoA, padded with zero weights)
     const double *u, *w;               // [3][Kp], [Kp]
-    const T *uT, *wT;
-    // state
-    T *phi, *face, *res, *dphi;
+    // per-cell / per-face state
     double *W, *q, *Wold, *fstate, *mface, *wallq, *macroF, *dW, *Wt, *ceq, *taut, *S,
         *cellres, *res12;
     // macro PR-SGS work: flux primitives (rho, U, rho E + p, p, rho E_rot) of the
@@ -67,6 +64,17 @@ struct Dev {
     unsigned int* bar;                   // grid-barrier state of the cooperative macro solve
     const int* col_off_d;                // colour offsets on the device (C + 1)
     int* status;
+};
+
+template <typename T>
+struct Dev : DevBase {
+    // R, Z, mu_ref, T_ref, omega_vis, omega0, omega1, delta in T (no conversions in kernels)
+    T tp[8];
+    T *slot_nT, *slot_AVT, *slot_dT, *slot_lsqT, *slot_sT;
+    T *fnT, *fsT;                      // face normal [3][F] and s_ij [F] in T
+    const T *uT, *wT;
+    // per-velocity state
+    T *phi, *face, *res, *dphi, *lstore;   // lstore: [2][N][Kp] frozen limiter values
 };
 
 // ------------------------------------------------------------------------------------
@@ -585,7 +593,11 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
         T L[2][NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) L[0][e] = L[1][e] = (limiter == 2) ? T(0) : T(1);
-        if (limiter == 1) {
+        if (limiter == 3) {
+            // frozen limiter values
+            vload(c.lstore + (size_t)i * c.Kp + k0, L[0]);
+            vload(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
+        } else if (limiter == 1 || limiter == 4) {
             // min over faces of Venkatakrishnan's psi = num/den, kept as a fraction
             // (den > 0) so that only the minimum is divided; capped at 1, threshold
             // eps^2 phi_i^2 relative to the cell value (readings)
@@ -611,6 +623,10 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
             }
 #pragma unroll
             for (int e = 0; e < NV; ++e) { L[0][e] = bn[0][e] / bd[0][e]; L[1][e] = bn[1][e] / bd[1][e]; }
+            if (limiter == 4) {
+                vstore(c.lstore + (size_t)i * c.Kp + k0, L[0]);
+                vstore(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
+            }
         }
         T ux[NV], uy[NV], uz[NV];
         vload(c.uT + k0, ux);
@@ -963,7 +979,13 @@ __global__ void k_iter_begin(Dev<T> c) {
         cfl = r < c.cfl_imp ? r : c.cfl_imp;
     }
     c.iterp[0] = cfl;
-    c.iterp[1] = (n < (double)c.first_order_iters) ? 2.0 : (double)c.limiter;
+    double mode = (n < (double)c.first_order_iters) ? 2.0 : (double)c.limiter;
+    // limiter freezing (reading; see rk_params.limiter_freeze)
+    if (mode == 1.0 && c.limiter_freeze > 0) {
+        if (n >= (double)c.limiter_freeze) mode = 3.0;
+        else if (n == (double)(c.limiter_freeze - 1)) mode = 4.0;
+    }
+    c.iterp[1] = mode;
 }
 
 template <typename T>

@@ -30,7 +30,11 @@ EXPORTS = ["rk_version", "rk_create", "rk_destroy", "rk_last_error", "rk_upload_
            "rk_bind_workspace", "rk_set_state_prim", "rk_set_state", "rk_get_distribution",
            "rk_implicit_iterate", "rk_residual", "rk_moments", "rk_surface", "rk_step",
            "rk_debug_get", "rk_profile", "rk_profile_get", "rk_residual_noalloc",
-           "rk_noalloc_last_error"]
+           "rk_noalloc_last_error", "rk_state_len", "rk_adjoint_workspace_size",
+           "rk_bind_adjoint_workspace", "rk_get_state", "rk_put_state", "rk_steady_residual",
+           "rk_vjp", "rk_objective", "rk_adjoint_solve", "rk_adjoint_get"]
+RK_OBJ_HEAT, RK_OBJ_DRAG = 0, 1
+OBJECTIVES = {"heat": RK_OBJ_HEAT, "drag": RK_OBJ_DRAG}
 PROF_CLASSES = ["recon", "face_interior", "face_boundary", "fluxes", "macro_sgs",
                 "micro_sweep_first", "micro_sweep_mid", "micro_sweep_last", "update"]
 
@@ -41,7 +45,8 @@ class RkParams(C.Structure):
                 ("omega1", C.c_double), ("delta", C.c_double), ("cfl_s", C.c_double),
                 ("cfl_imp", C.c_double), ("cfl_imp0", C.c_double), ("cfl_ramp", C.c_double),
                 ("lim_k", C.c_double), ("n_micro_sgs", C.c_int32), ("n_macro_sgs", C.c_int32),
-                ("limiter", C.c_int32), ("first_order_iters", C.c_int32)]
+                ("limiter", C.c_int32), ("first_order_iters", C.c_int32),
+                ("limiter_freeze", C.c_int32)]
 
 
 _lib = None
@@ -81,6 +86,16 @@ def load(path: str | None = None):
         "rk_profile_get": ([vp, vp, vp], C.c_int),
         "rk_residual_noalloc": ([vp, vp, i64, vp, C.c_size_t], C.c_int),
         "rk_noalloc_last_error": ([], C.c_char_p),
+        "rk_state_len": ([vp, P(i64)], C.c_int),
+        "rk_adjoint_workspace_size": ([vp, i32, P(sz)], C.c_int),
+        "rk_bind_adjoint_workspace": ([vp, i32, vp, sz], C.c_int),
+        "rk_get_state": ([vp, vp, C.c_int], C.c_int),
+        "rk_put_state": ([vp, vp, C.c_int], C.c_int),
+        "rk_steady_residual": ([vp, vp, C.c_int], C.c_int),
+        "rk_vjp": ([vp, vp, vp, vp, C.c_int], C.c_int),
+        "rk_objective": ([vp, C.c_int, vp, vp, vp, C.c_int], C.c_int),
+        "rk_adjoint_solve": ([vp, C.c_int, i32, dp, P(i32), vp, vp, vp], C.c_int),
+        "rk_adjoint_get": ([vp, vp, C.c_int], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -259,3 +274,102 @@ class Solver:
         res = np.zeros(6)
         self._check(self.L.rk_residual(self.h, _ptr(res)))
         return res
+
+    # ---- adjoint of the steady residual (FP64 solvers) ------------------------------
+    def bind_adjoint(self, krylov_dim: int = 20):
+        """Allocate (torch) and bind the adjoint workspace; krylov_dim = GMRES restart."""
+        torch = self.torch
+        nbytes = C.c_size_t()
+        self._check(self.L.rk_adjoint_workspace_size(self.h, int(krylov_dim), C.byref(nbytes)))
+        self.adj_workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        self._check(self.L.rk_bind_adjoint_workspace(self.h, int(krylov_dim), _ptr(self.adj_workspace),
+                                                     int(nbytes.value)))
+        n = C.c_int64()
+        self._check(self.L.rk_state_len(self.h, C.byref(n)))
+        self.state_len = int(n.value)
+
+    def _vec(self, x):
+        """(pointer, on_device) of a packed state vector (numpy or CUDA tensor)."""
+        if hasattr(x, "data_ptr"):
+            return _ptr(x), 1
+        return _ptr(x), 0
+
+    def get_state(self):
+        x = np.empty(self.state_len)
+        self._check(self.L.rk_get_state(self.h, _ptr(x), 0))
+        return x
+
+    def put_state(self, x):
+        x = x if hasattr(x, "data_ptr") else _c(x, np.float64)
+        p, dev = self._vec(x)
+        self._check(self.L.rk_put_state(self.h, p, dev))
+
+    def steady_residual(self):
+        r = np.empty(self.state_len)
+        self._check(self.L.rk_steady_residual(self.h, _ptr(r), 0))
+        return r
+
+    def vjp(self, v):
+        """(dR/dX)^T v and (dR/dp)^T v at the current state."""
+        v = v if hasattr(v, "data_ptr") else _c(v, np.float64)
+        out = np.empty(self.state_len) if not hasattr(v, "data_ptr") else self.torch.empty_like(v)
+        pp = np.zeros(6)
+        pv, dev = self._vec(v)
+        self._check(self.L.rk_vjp(self.h, pv, _ptr(out), _ptr(pp), dev))
+        return out, pp
+
+    def objective(self, which="heat"):
+        """J, dJ/dX (packed) and the explicit dJ/dp at the current state."""
+        J = np.zeros(1); g = np.empty(self.state_len); dp = np.zeros(6)
+        self._check(self.L.rk_objective(self.h, OBJECTIVES[which], _ptr(J), _ptr(g), _ptr(dp), 0))
+        return float(J[0]), g, dp
+
+    def adjoint_solve(self, which="heat", max_iter: int = 500, tol: float = 1e-10):
+        """Adjoint solve at the current state: (iterations, relative residual, J, dJ/dp)."""
+        it = C.c_int32(0); rr = np.zeros(1); J = np.zeros(1); dp = np.zeros(6)
+        self._check(self.L.rk_adjoint_solve(self.h, OBJECTIVES[which], int(max_iter), float(tol),
+                                            C.byref(it), _ptr(rr), _ptr(J), _ptr(dp)))
+        return int(it.value), float(rr[0]), float(J[0]), dp
+
+    def adjoint_get(self):
+        lam = np.empty(self.state_len)
+        self._check(self.L.rk_adjoint_get(self.h, _ptr(lam), 0))
+        return lam
+
+    def set_boundary_params(self, p):
+        """Apply p = (T_w shift, rho_inf, U_inf[3], T_inf) to the boundary conditions of
+        the workload (walls: T + p[0]; farfields: (p[1], p[2:5], p[5]))."""
+        p = [float(x) for x in p]
+        for b, bc in enumerate(self.wl.bcs):
+            if bc.kind == RK_WALL:
+                U = _c(bc.U, np.float64)
+                self._check(self.L.rk_set_bc(self.h, b, RK_WALL, float(bc.rho), _ptr(U), float(bc.T) + p[0]))
+            else:
+                U = _c(p[2:5], np.float64)
+                self._check(self.L.rk_set_bc(self.h, b, RK_FARFIELD, p[1], _ptr(U), p[5]))
+
+
+def steady_objective(solver: Solver, p, which="heat", n_iter: int = 2000, tol: float = 1e-12,
+                     adj_iter: int = 500, adj_tol: float = 1e-10):
+    """J(X*(p)) of the converged steady state as a differentiable torch function of
+    the boundary parameters p (6 doubles: T_w shift, rho_inf, U_inf, T_inf): forward =
+    implicit iterations to convergence; backward = the adjoint solve (dJ/dp)."""
+    import torch
+
+    class _SteadyJ(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, pt):
+            solver.set_boundary_params(pt.detach().cpu().numpy())
+            rc, done, res = solver.iterate(n_iter, tol)
+            if rc != RK_OK:
+                raise RykovError(rc, "steady_objective: the iteration diverged")
+            it, rel, J, dJdp = solver.adjoint_solve(which, adj_iter, adj_tol)
+            ctx.save_for_backward(torch.as_tensor(dJdp, dtype=pt.dtype))
+            return pt.new_tensor(J)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (dJdp,) = ctx.saved_tensors
+            return gout * dJdp.to(gout.device)
+
+    return _SteadyJ.apply(p)

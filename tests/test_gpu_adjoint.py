@@ -1,0 +1,203 @@
+"""Parity of the CUDA adjoint (through the C ABI) with the PyTorch-autograd oracle of the
+steady residual operator (oracle/adjoint.py).
+
+Tolerance: FP64, 1e-10 relative to the largest entry of each compared block.  The
+steady residual and its VJP are sums of a few hundred terms per entry, evaluated in
+a different order on each side; the limiter's min/max choices are taken on values
+that agree to ~1e-16, far from a tie on these seeded states.  The adjoint solve is
+compared at the tolerance the GMRES is run to.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.adjoint import DRAG, HEAT, Steady
+from paper_2303_10846_gb300 import inputs as I
+from tests import workloads as TW
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def lid_farfield():
+    wl = TW.tiny_cavity()
+    wl.bcs = [wl.bcs[0], I.BC(I.BC_FARFIELD, 1.05, (0.15, 0.02, -0.03), 1.1)]
+    return wl
+
+
+def tet():
+    wl = TW.tiny_tet(n_gh=5, lim=1, cfl_imp=20.0)       # K = 125: ragged tail of 32
+    wl.params = dataclasses.replace(wl.params, first_order_iters=0)
+    return wl
+
+
+WORKLOADS = {"lid_farfield": lid_farfield, "tet": tet}
+
+
+def _solver_prec(wl, prec, m):
+    from paper_2303_10846_gb300.rykov import Solver
+    s = Solver(wl, prec)
+    s.bind_adjoint(m)
+    return s
+
+
+def _solver(wl, m=20):
+    return _solver_prec(wl, "fp64", m)
+
+
+def _blocks(st, x):
+    n1 = 2 * st.N * st.K
+    return x[:n1], x[n1:n1 + 6 * st.N], x[n1 + 6 * st.N:]
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_steady_residual_vjp_and_objectives(name):
+    wl = WORKLOADS[name]()
+    s = _solver(wl)
+    s.iterate(4)
+    x = s.get_state()
+    st = Steady(wl)
+    xt = torch.as_tensor(x)
+    # state round trip through the ABI
+    s.put_state(x)
+    assert np.array_equal(s.get_state(), x)
+    # R(X; p): the blocks are differences of O(1) terms (collision and flux, moments
+    # and the state), so the error is measured on the scale of those terms
+    r_gpu = s.steady_residual()
+    r_orc = st.R_flat(xt, st.p0()).numpy()
+    phi, W, q = st.unpack(xt)
+    Fm, _ = st.micro_flux(phi, st.p0())
+    scales = (float(Fm.abs().max()), float(W.abs().max()), float(W.abs().max()))
+    for a, b, sc in zip(_blocks(st, r_gpu), _blocks(st, r_orc), scales):
+        assert np.max(np.abs(a - b)) < TOL * sc
+    # (dR/dX)^T v and (dR/dp)^T v for a seeded v
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(x.size)
+    out, pp = s.vjp(v)
+    ot, pt = st.vjp(xt, torch.as_tensor(v))
+    for a, b in zip(_blocks(st, out), _blocks(st, ot.numpy())):
+        assert _rel(a, b) < TOL
+    assert _rel(pp, pt.numpy()) < TOL
+    # objectives: J, dJ/dX, dJ/dp|_X
+    for which, code in (("heat", HEAT), ("drag", DRAG)):
+        J, g, dp = s.objective(which)
+        Jt, gt, dpt = st.objective_grad(xt, code)
+        assert abs(J - Jt) <= 1e-12 * abs(Jt)
+        assert _rel(g, gt.numpy()) < TOL
+        assert _rel(dp, dpt.numpy()) < TOL
+
+
+def test_vjp_is_linear_and_padding_free():
+    """(dR/dX)^T (a v + b w) = a (dR/dX)^T v + b (dR/dX)^T w, and repeated calls give
+    identical bits (fixed-order gathers, no atomics)."""
+    wl = tet()
+    s = _solver(wl)
+    s.iterate(3)
+    rng = np.random.default_rng(3)
+    v, w = rng.standard_normal(s.state_len), rng.standard_normal(s.state_len)
+    ov, _ = s.vjp(v)
+    ow, _ = s.vjp(w)
+    ovw, _ = s.vjp(2.0 * v - 3.0 * w)
+    assert _rel(ovw, 2.0 * ov - 3.0 * ow) < 1e-12
+    ov2, _ = s.vjp(v)
+    assert np.array_equal(ov, ov2)
+
+
+def test_adjoint_solve_matches_dense_oracle():
+    """Converged steady state on the GPU, GMRES adjoint on the GPU; the oracle solves
+    the same transposed system densely at the GPU's state."""
+    wl = lid_farfield()
+    s = _solver(wl, m=30)
+    rc, n, res = s.iterate(3000, 1e-13)
+    assert rc == 0 and np.max(res) < 1e-13
+    x = s.get_state()
+    st = Steady(wl)
+    xt = torch.as_tensor(x)
+    A = st.jacobian(xt).numpy()
+    for which, code in (("heat", HEAT), ("drag", DRAG)):
+        it, rel, J, dJdp = s.adjoint_solve(which, max_iter=400, tol=1e-11)
+        assert rel <= 1e-11, (which, it, rel)
+        Jt, jx, jp = st.objective_grad(xt, code)
+        lam_t = np.linalg.solve(A.T, -jx.numpy())
+        _, rp = st.vjp(xt, torch.as_tensor(lam_t))
+        dJdp_t = (jp + rp).numpy()
+        lam = s.adjoint_get()
+        assert _rel(lam, lam_t) < 1e-7
+        assert _rel(dJdp, dJdp_t) < 1e-8
+        assert abs(J - Jt) <= 1e-12 * abs(Jt)
+        # warm start: a second call at the same state converges at once
+        it2, rel2, _, dJdp2 = s.adjoint_solve(which, max_iter=400, tol=1e-11)
+        assert it2 == 0 and rel2 <= 1e-11
+        assert _rel(dJdp2, dJdp) < 1e-12
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    from paper_2303_10846_gb300.rykov import steady_objective
+    wl = lid_farfield()
+    s = _solver(wl, m=30)
+    st = Steady(wl)
+    p = st.p0().clone().requires_grad_(True)
+    J = steady_objective(s, p, "heat", n_iter=3000, tol=1e-13, adj_iter=400, adj_tol=1e-11)
+    J.backward()
+    _, _, J2, dJdp = s.adjoint_solve("heat", max_iter=400, tol=1e-11)
+    assert abs(float(J) - J2) <= 1e-12 * abs(J2)
+    assert _rel(p.grad.numpy(), dJdp) < 1e-12
+
+
+def test_adjoint_of_a_mixed_precision_context():
+    """A mixed context's adjoint is the FP64 adjoint at its (FP32-distribution) state:
+    VJP parity with the oracle at that state, and dJ/dp close to the FP64 context's
+    (the two steady states differ at the mixed-precision level)."""
+    wl = lid_farfield()
+    sm = _solver_prec(wl, "mixed", 30)
+    rc, n, res = sm.iterate(400, 1e-9)
+    assert rc == 0
+    x = sm.get_state()
+    st = Steady(wl)
+    xt = torch.as_tensor(x)
+    v = np.random.default_rng(4).standard_normal(x.size)
+    out, pp = sm.vjp(v)
+    ot, pt = st.vjp(xt, torch.as_tensor(v))
+    for a, b in zip(_blocks(st, out), _blocks(st, ot.numpy())):
+        assert _rel(a, b) < TOL
+    it, rel, J, dJdp = sm.adjoint_solve("heat", max_iter=400, tol=1e-10)
+    assert rel <= 1e-10
+    s64 = _solver(wl, 30)
+    s64.iterate(3000, 1e-13)
+    _, _, J64, dJdp64 = s64.adjoint_solve("heat", max_iter=400, tol=1e-10)
+    assert abs(J - J64) <= 1e-4 * abs(J64)
+    assert _rel(dJdp, dJdp64) < 1e-4
+
+
+def test_vjp_with_frozen_limiter():
+    """After the iteration froze the limiter, the steady operator and its VJP use the
+    stored limiter values as constants (the oracle is given the C oracle's values,
+    computed from a state equal to the GPU's to round-off)."""
+    import oracle as O
+    wl = tet()
+    wl.params = dataclasses.replace(wl.params, limiter_freeze=5)
+    o = O.Oracle(wl)
+    o.iterate(8)
+    s = _solver(wl)
+    s.iterate(8)
+    x = s.get_state()
+    xt = torch.as_tensor(x)
+    st = Steady(wl, L_frozen=o.get(O.BUF_LSTORE))
+    r_gpu = s.steady_residual()
+    r_orc = st.R_flat(xt, st.p0()).numpy()
+    phi, W, q = st.unpack(xt)
+    Fm, _ = st.micro_flux(phi, st.p0())
+    assert np.max(np.abs(r_gpu[:2 * st.N * st.K] - r_orc[:2 * st.N * st.K])) < 1e-9 * float(Fm.abs().max())
+    v = np.random.default_rng(2).standard_normal(x.size)
+    out, pp = s.vjp(v)
+    ot, pt = st.vjp(xt, torch.as_tensor(v))
+    for a, b in zip(_blocks(st, out), _blocks(st, ot.numpy())):
+        assert _rel(a, b) < 1e-9

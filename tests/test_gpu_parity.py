@@ -156,3 +156,19 @@ def test_launch_schemes_give_identical_results(env, monkeypatch):
     b.iterate(4)
     Wb, qb, _ = b.moments()
     assert np.array_equal(Wa, Wb) and np.array_equal(qa, qb)
+
+
+def test_limiter_freeze_fp64():
+    """Iterations after the limiter is frozen (reading: the limiter values of iteration
+    limiter_freeze - 1 are reused) match the oracle's frozen iteration."""
+    import dataclasses
+    wl = TW.tiny_tet(n_gh=5, lim=1, cfl_imp=20.0)
+    wl.params = dataclasses.replace(wl.params, first_order_iters=2, limiter_freeze=6)
+    o = O.Oracle(wl)
+    s = _solver(wl, debug=False)
+    o.iterate(20)
+    s.iterate(20)
+    assert _rel(s.debug_get("PHI"), o.get(O.BUF_PHI)) < TOL64
+    W, q, _ = s.moments()
+    assert _rel(W, o.get(O.BUF_W)) < TOL64
+    assert _rel(q, o.get(O.BUF_Q)) < 1e-9
