@@ -135,7 +135,7 @@ def dvs_sample(wl, stride):
     return w2
 
 
-def cpu_oracle_rate(wl, iters=1, stride=10):
+def cpu_oracle_rate(wl, iters=4, stride=2):
     """Oracle (FP64 C, OpenMP over cells/faces) on the host cores: updates/s on a
     DVS sample of the workload, the first `iters` implicit iterations."""
     import oracle as O
