@@ -172,6 +172,12 @@ enum {
  * [N][6], DT [N][3] (CFL step, implicit step, eps^2), S [F], TAUT [N].
  * `count` is the number of doubles the caller's buffer holds. */
 int rk_debug_get(rk_ctx* ctx, int which, double* host_out, int64_t count);
+/* Selected rows of a distribution-shaped verification buffer, for checks of large
+ * cases one cell or face at a time: which = RK_BUF_PHI, RK_BUF_RES, RK_BUF_DPHI,
+ * RK_BUF_MICRO_F (rows = cell indices) or RK_BUF_FACE (rows = face indices);
+ * host_out[2][n_rows][K] doubles (field, row, velocity).  RK_BUF_MICRO_F needs a
+ * context created with RK_DEBUG.  RK_EINVAL for a row out of range. */
+int rk_debug_rows(rk_ctx* ctx, int which, const int64_t* rows, int64_t n_rows, double* host_out);
 
 /* ---- per-kernel timing ----------------------------------------------------------
  * rk_profile(ctx, 1) makes the library bracket each kernel class below with CUDA

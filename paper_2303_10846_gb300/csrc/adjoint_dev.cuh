@@ -613,17 +613,28 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs 
             if (limiter == 3) {
                 L = c.lstore[fd * NK + (size_t)i * c.Kp + k];     // frozen: a constant
             } else if (limiter == 1) {
-                double bn = 1.0, bd = 1.0;
-                const double ep = eps2 * pc * pc;
+                // the forward kernel's minimum: psi at the face of largest d2 (with
+                // Delta_max) and at the face of smallest d2 (with Delta_min)
+                double d2hi = 0.0, d2lo = 0.0;
+                int qhi = -1, qlo = -1;
                 for (int q = 0; q < ns; ++q) {
                     const double d2 = g[0] * s_d[wp][0][q] + g[1] * s_d[wp][1][q] + g[2] * s_d[wp][2][q];
-                    if (d2 == 0.0) continue;
-                    const double d1 = d2 > 0.0 ? dmax : dmin;
+                    if (d2 > d2hi) { d2hi = d2; qhi = q; }
+                    if (d2 < d2lo) { d2lo = d2; qlo = q; }
+                }
+                const double ep = eps2 * pc * pc;
+                if (qhi >= 0) {
+                    const double d1 = dmax, d2 = d2hi;
                     const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
                     const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
-                    if (nu * bd < bn * de) { bn = nu; bd = de; lq = q; }
+                    if (nu < de) { L = nu / de; lq = qhi; }
                 }
-                L = bn / bd;
+                if (qlo >= 0) {
+                    const double d1 = dmin, d2 = d2lo;
+                    const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
+                    const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
+                    if (nu < L * de) { L = nu / de; lq = qlo; }
+                }
             }
             // adjoint of phi0 gathered over the faces where this cell is upwind
             double self = 0.0, Gb[3] = {0.0, 0.0, 0.0};

@@ -277,6 +277,9 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.cellres = cv.take<double>(12 * N); d.res12 = cv.take<double>(16);
     d.mPc = cv.take<double>(8 * N); d.mDb = cv.take<double>(4 * N);
     d.sG0 = cv.take<double>(6 * nnz); d.sC = cv.take<double>(2 * nnz);
+    d.pos_off = cv.take<int>(N + 1); d.cell_pos = cv.take<int>(N);
+    d.pslot_nbr = cv.take<int>(nnz); d.pslot_ncol = cv.take<int>(nnz);
+    d.pslot_n = cv.take<double>(3 * nnz);
     d.bar = cv.take<unsigned int>(4);
     d.col_off_d = cv.take<int>(ctx->C + 1);
     d.status = cv.take<int>(4);
@@ -350,6 +353,30 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
     CK(h2d(d.uT, uTs.data(), 3 * Kp * sizeof(T)));
     CK(h2d(d.wT, wTs.data(), Kp * sizeof(T)));
     CK(h2d(ctx->sched.col_cell, ctx->col_cell.data(), N * 4));
+    {
+        // slots in colour-position order for the macro PR-SGS
+        std::vector<int> pos_off(N + 1, 0), cell_pos(N), pnbr(nnz), pncol(nnz);
+        std::vector<double> pn(3 * nnz);
+        int mp = 0;
+        for (size_t p = 0; p < N; ++p) {
+            const int i = ctx->col_cell[p];
+            cell_pos[i] = (int)p;
+            pos_off[p] = mp;
+            for (int m = ctx->slot_off[i]; m < ctx->slot_off[i + 1]; ++m, ++mp) {
+                pnbr[mp] = ctx->slot_nbr[m];
+                pncol[mp] = ctx->slot_ncol[m];
+                const double sg = ctx->slot_left[m] ? 1.0 : -1.0;
+                for (int r = 0; r < 3; ++r) pn[(size_t)r * nnz + mp] = sg * ctx->slot_n[(size_t)r * nnz + m];
+            }
+        }
+        pos_off[N] = mp;
+        CK(h2d(d.pos_off, pos_off.data(), (N + 1) * 4));
+        CK(h2d(d.cell_pos, cell_pos.data(), N * 4));
+        CK(h2d(d.pslot_nbr, pnbr.data(), nnz * 4));
+        CK(h2d(d.pslot_ncol, pncol.data(), nnz * 4));
+        CK(h2d(d.pslot_n, pn.data(), 3 * nnz * 8));
+        CK(cudaStreamSynchronize(s));
+    }
     CK(h2d(d.col_off_d, ctx->col_off.data(), (ctx->C + 1) * 4));
     CK(cudaMemsetAsync(d.bar, 0, 4 * sizeof(unsigned int), s));
     ctx->sched.col_off = ctx->col_off;
@@ -720,6 +747,46 @@ static int debug_impl(rk_ctx* ctx, rk::Dev<T>& d, int which, double* out, int64_
         }
         default: return fail(ctx, RK_EINVAL, "rk_debug_get: unknown buffer");
     }
+}
+
+template <typename T>
+static int debug_rows_impl(rk_ctx* ctx, rk::Dev<T>& d, int which, const int64_t* rows, int64_t n, double* out) {
+    const size_t N = ctx->N, F = ctx->F, K = ctx->K, Kp = ctx->Kp;
+    const T* src = nullptr;
+    size_t nrows = N;
+    switch (which) {
+        case RK_BUF_PHI: src = d.phi; break;
+        case RK_BUF_RES: src = d.res; break;
+        case RK_BUF_DPHI: src = d.dphi; break;
+        case RK_BUF_FACE: src = d.face; nrows = F; break;
+        case RK_BUF_MICRO_F: {
+            if (!ctx->dbg) return fail(ctx, RK_ESTATE, "rk_debug_rows: context not created with the debug flag");
+            cudaError_t e = rk::Launch<T>::debug_micro_flux(d, ctx->stream, (T*)ctx->dbg);
+            if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+            src = (const T*)ctx->dbg;
+            break;
+        }
+        default: return fail(ctx, RK_EINVAL, "rk_debug_rows: unsupported buffer");
+    }
+    for (int64_t r = 0; r < n; ++r)
+        if (rows[r] < 0 || (size_t)rows[r] >= nrows) return fail(ctx, RK_EINVAL, "rk_debug_rows: row out of range");
+    std::vector<T> tmp(2 * (size_t)n * Kp);
+    for (int fd = 0; fd < 2; ++fd)
+        for (int64_t r = 0; r < n; ++r)
+            CK(cudaMemcpyAsync(tmp.data() + ((size_t)fd * n + r) * Kp, src + ((size_t)fd * nrows + rows[r]) * Kp,
+                               Kp * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t q = 0; q < 2 * (size_t)n; ++q)
+        for (size_t k = 0; k < K; ++k) out[q * K + k] = (double)tmp[q * Kp + k];
+    return RK_OK;
+}
+
+extern "C" int rk_debug_rows(rk_ctx* ctx, int which, const int64_t* rows, int64_t n_rows, double* host_out) {
+    int rc = need_bound(ctx, "rk_debug_rows");
+    if (rc) return rc;
+    if (!host_out || !rows || n_rows < 0) return fail(ctx, RK_EINVAL, "rk_debug_rows: bad arguments");
+    return ctx->prec == RK_FP64 ? debug_rows_impl(ctx, ctx->dd, which, rows, n_rows, host_out)
+                                : debug_rows_impl(ctx, ctx->df, which, rows, n_rows, host_out);
 }
 
 extern "C" int rk_debug_get(rk_ctx* ctx, int which, double* host_out, int64_t count) {

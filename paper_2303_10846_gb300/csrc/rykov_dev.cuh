@@ -17,6 +17,23 @@
 namespace rk {
 
 constexpr int MAXF = 8;        // faces per cell
+// micro sweep tuning: faces per load group, velocities per lane in the middle sweeps
+// (mixed mode), minimum resident blocks of the first / middle / last sweeps
+#ifndef MICRO_PF
+#define MICRO_PF 1
+#endif
+#ifndef MICRO_MID_NV
+#define MICRO_MID_NV 4
+#endif
+#ifndef MICRO_FIRST_MINB
+#define MICRO_FIRST_MINB 3
+#endif
+#ifndef MICRO_MID_MINB
+#define MICRO_MID_MINB 4
+#endif
+#ifndef MICRO_LAST_MINB
+#define MICRO_LAST_MINB 4
+#endif
 constexpr int EQN = 24;        // constants of one Rykov equilibrium (see make_eq)
 constexpr int CEQ = 28;        // per-cell record: EQN constants, 1/tau~, diagonal base
 constexpr int FST = 16;        // face state record
@@ -61,6 +78,13 @@ struct DevBase {
     // current iterate per cell, diagonal base per cell, per-slot Euler flux of the
     // neighbour's W^n and the coefficients A/(2V), A r/(2V)
     double *mPc, *mDb, *sG0, *sC;        // mDb: [N][4] = 1/D, 1/(D + 1/(Z tau)), 1/(Z tau)
+    // the slots again, ordered by colour position (cells in col_cell order), so that a
+    // macro point update finds its slot range from its position without first loading
+    // the cell index: slot base per position [N+1], position of each cell [N],
+    // neighbour, neighbour colour [nnz], outward normal [3][nnz]; sG0 and sC are
+    // indexed by these position-ordered slots
+    const int *pos_off, *cell_pos, *pslot_nbr, *pslot_ncol;
+    const double* pslot_n;
     unsigned int* bar;                   // grid-barrier state of the cooperative macro solve
     const int* col_off_d;                // colour offsets on the device (C + 1)
     int* status;
@@ -598,12 +622,14 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
             vload(c.lstore + (size_t)i * c.Kp + k0, L[0]);
             vload(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
         } else if (limiter == 1 || limiter == 4) {
-            // min over faces of Venkatakrishnan's psi = num/den, kept as a fraction
-            // (den > 0) so that only the minimum is divided; capped at 1, threshold
-            // eps^2 phi_i^2 relative to the cell value (readings)
-            T bn[2][NV], bd[2][NV];
+            // min over faces of Venkatakrishnan's psi(d1, d2), capped at 1, threshold
+            // eps^2 phi_i^2 relative to the cell value (readings).  psi < 1 needs
+            // y = d2/d1 > 1/2, where psi decreases in y; so the minimum over the faces
+            // with d2 > 0 is psi(Delta_max, max d2) and over d2 < 0 psi(Delta_min, min d2):
+            // two evaluations instead of one per face (the same value up to rounding)
+            T d2hi[2][NV], d2lo[2][NV];
 #pragma unroll
-            for (int e = 0; e < NV; ++e) bn[0][e] = bn[1][e] = bd[0][e] = bd[1][e] = T(1);
+            for (int e = 0; e < NV; ++e) d2hi[0][e] = d2hi[1][e] = d2lo[0][e] = d2lo[1][e] = T(0);
 #pragma unroll 1
             for (int q = 0; q < ns; ++q) {
                 const T dx = s_d[w][0][q], dy = s_d[w][1][q], dz = s_d[w][2][q];
@@ -612,17 +638,31 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
 #pragma unroll
                     for (int fd = 0; fd < 2; ++fd) {
                         const T d2 = g[fd][0][e] * dx + g[fd][1][e] * dy + g[fd][2][e] * dz;
-                        if (d2 == T(0)) continue;
-                        const T d1 = d2 > T(0) ? dmax[fd][e] : dmin[fd][e];
-                        const T ph0 = fd == 0 ? pg[e] : ph[e];
-                        const T ep = eps2 * ph0 * ph0;      // threshold relative to the cell value
-                        const T num = d1 * d1 + ep + T(2) * d1 * d2;
-                        const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
-                        if (num * bd[fd][e] < bn[fd][e] * den) { bn[fd][e] = num; bd[fd][e] = den; }
+                        d2hi[fd][e] = d2 > d2hi[fd][e] ? d2 : d2hi[fd][e];
+                        d2lo[fd][e] = d2 < d2lo[fd][e] ? d2 : d2lo[fd][e];
                     }
             }
 #pragma unroll
-            for (int e = 0; e < NV; ++e) { L[0][e] = bn[0][e] / bd[0][e]; L[1][e] = bn[1][e] / bd[1][e]; }
+            for (int e = 0; e < NV; ++e)
+#pragma unroll
+                for (int fd = 0; fd < 2; ++fd) {
+                    const T ph0 = fd == 0 ? pg[e] : ph[e];
+                    const T ep = eps2 * ph0 * ph0;
+                    T Lv = T(1);
+                    if (d2hi[fd][e] > T(0)) {
+                        const T d1 = dmax[fd][e], d2 = d2hi[fd][e];
+                        const T num = d1 * d1 + ep + T(2) * d1 * d2;
+                        const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
+                        if (num < den) Lv = num / den;
+                    }
+                    if (d2lo[fd][e] < T(0)) {
+                        const T d1 = dmin[fd][e], d2 = d2lo[fd][e];
+                        const T num = d1 * d1 + ep + T(2) * d1 * d2;
+                        const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
+                        if (num < Lv * den) Lv = num / den;
+                    }
+                    L[fd][e] = Lv;
+                }
             if (limiter == 4) {
                 vstore(c.lstore + (size_t)i * c.Kp + k0, L[0]);
                 vstore(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
@@ -995,16 +1035,18 @@ __global__ void k_macro_prep(Dev<T> c) {
     const double cfl = c.iterp[0];
     const double iv = 1.0 / c.vol[i];
     double D = 1.0 / (cfl * c.dt[i]);
+    const int ps = c.pos_off[c.cell_pos[i]];
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
         const int f = c.slot_face[m], j = c.slot_nbr[m];
+        const size_t mp = (size_t)(ps + m - c.slot_off[i]);
         const double A = c.fa[f] * iv;
         D += 0.5 * A * c.rf[f];
-        c.sC[2 * (size_t)m] = 0.5 * A;
-        c.sC[2 * (size_t)m + 1] = 0.5 * A * c.rf[f];
+        c.sC[2 * mp] = 0.5 * A;
+        c.sC[2 * mp + 1] = 0.5 * A * c.rf[f];
         if (j >= 0) {
             const double sg = c.slot_left[m] ? 1.0 : -1.0;
             euler_flux(c.W + 6 * (size_t)j, sg * c.fn[f], sg * c.fn[c.F + f], sg * c.fn[2 * c.F + f],
-                       c.sG0 + 6 * (size_t)m);
+                       c.sG0 + 6 * mp);
         }
     }
     const Prim p = prim_from_W(c.W + 6 * (size_t)i, c.R);
@@ -1024,15 +1066,20 @@ __global__ void k_macro_prep(Dev<T> c) {
 // primitives; rho~ R T~ of the rotational source from the cell's current iterate.
 // An update whose predicted state is not admissible (rho, T_tr or T_rot not
 // positive) is skipped.
+// MACRO_LANES threads share one cell: each takes every MACRO_LANES-th face, and the
+// partial sums are combined by a butterfly within the group (every lane of the group
+// ends with the same bits, lane 0 stores).
+#ifndef MACRO_LANES
+#define MACRO_LANES 2
+#endif
 template <typename T>
-__device__ __forceinline__ void macro_point(const Dev<T>& c, int i, int colour, int first_forward) {
+__device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int colour, int first_forward,
+                                            int g) {
     double o[6] = {0, 0, 0, 0, 0, 0};
-    for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
-        const int j = c.slot_nbr[m];
-        if (j < 0 || (first_forward && c.slot_ncol[m] > colour)) continue;
-        const int f = c.slot_face[m];
-        const double sg = c.slot_left[m] ? 1.0 : -1.0;
-        const double nx = sg * c.fn[f], ny = sg * c.fn[c.F + f], nz = sg * c.fn[2 * c.F + f];
+    for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += MACRO_LANES) {
+        const int j = c.pslot_nbr[m];
+        if (j < 0 || (first_forward && c.pslot_ncol[m] > colour)) continue;
+        const double nx = c.pslot_n[m], ny = c.pslot_n[c.nnz + m], nz = c.pslot_n[2 * c.nnz + m];
         // the iterate of neighbours is read through L2: in the cooperative solve it was
         // written by other blocks during this kernel
         double P[8], dWj[6];
@@ -1048,6 +1095,14 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int i, int colour, 
         const double c1 = c.sC[2 * (size_t)m], c2 = c.sC[2 * (size_t)m + 1];
 #pragma unroll
         for (int q = 0; q < 6; ++q) o[q] += c1 * (G1[q] - G0[q]) - c2 * dWj[q];
+    }
+    if (MACRO_LANES > 1) {
+        const unsigned mask = MACRO_LANES == 32 ? 0xffffffffu
+                                                : ((1u << MACRO_LANES) - 1u) << ((threadIdx.x & 31) & ~(MACRO_LANES - 1));
+#pragma unroll
+        for (int off = 1; off < MACRO_LANES; off <<= 1)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) o[q] += __shfl_xor_sync(mask, o[q], off);
     }
     const double* W = c.W + 6 * (size_t)i;
     double* dW = c.dW + 6 * (size_t)i;
@@ -1065,17 +1120,17 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int i, int colour, 
     cand[5] = ((rRT - W[5]) * izt - F[5] - o[5]) * iDr;
     double Wn[6], Pn[8];
     for (int q = 0; q < 6; ++q) Wn[q] = W[q] + cand[q];
-    if (!flux_prim(Wn, Pn)) return;
+    if (!flux_prim(Wn, Pn) || g != 0) return;
     for (int q = 0; q < 6; ++q) __stcg(dW + q, cand[q]);
     for (int q = 0; q < 8; ++q) __stcg(c.mPc + 8 * (size_t)i + q, Pn[q]);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* cells, int n, int colour,
+__global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* col_cell, int lo, int n, int colour,
                                                      int first_forward) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    macro_point(c, cells[t], colour, first_forward);
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
+    if (t >= n) return;                           // whole lane group
+    macro_point(c, lo + t, col_cell[lo + t], colour, first_forward, (int)(threadIdx.x % MACRO_LANES));
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1120,15 +1175,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status) {
 template <typename T>
 __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cell, const int* col_off,
                                                     int C, int n_macro, unsigned int* bar) {
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = (gridDim.x * blockDim.x) / MACRO_LANES;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
+    const int g = (int)(threadIdx.x % MACRO_LANES);
     for (int it = 0; it < n_macro; ++it) {
         for (int dir = 0; dir < 2; ++dir) {
             for (int cc = 0; cc < C; ++cc) {
                 const int col = dir == 0 ? cc : C - 1 - cc;
                 const int lo = col_off[col], hi = col_off[col + 1];
                 const int ff = (it == 0 && dir == 0);
-                for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += stride)
-                    macro_point(c, col_cell[t], col, ff);
+                for (int t = lo + gid; t < hi; t += stride) macro_point(c, t, col_cell[t], col, ff, g);
                 if (!grid_barrier(bar, c.status)) return;
             }
         }
@@ -1169,12 +1225,14 @@ __global__ void k_macro_finish(Dev<T> c) {
 // sums) are separate instantiations, so that the middle sweeps carry neither the
 // face reads nor the twelve accumulators
 template <typename T, int WPB, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? 2 : (FIRST ? 3 : 4)))
+__global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_LAST_MINB : (FIRST ? MICRO_FIRST_MINB : MICRO_MID_MINB)))
     k_micro_sweep(Dev<T> c, const int* cells, int ncells, int colour) {
     constexpr bool first = FIRST, last = LAST, first_forward = FIRST;
     using R = Red<T>;
     // velocities per lane: 16-byte accesses in the middle sweeps of the mixed mode
-    constexpr int NV = (sizeof(T) == 4 && !FIRST && !LAST) ? 4 : VW<T>::N;
+    constexpr int NV = (sizeof(T) == 4 && !FIRST && !LAST) ? MICRO_MID_NV : VW<T>::N;
+    // faces whose loads are issued together
+    constexpr int PF = MICRO_PF;
     __shared__ T s_e[WPB][EQN + 2];
     __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_ok[WPB][MAXF];
     __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
@@ -1209,38 +1267,55 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? 2 : (FI
         T D[NV], og[NV], oh[NV], Fg[NV], Fh[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { D[q] = base; og[q] = oh[q] = Fg[q] = Fh[q] = T(0); }
+        // faces in groups of PF: all loads of a group are issued before its arithmetic,
+        // so that PF neighbour rows are in flight per thread (the accumulation order
+        // over the faces is unchanged)
 #pragma unroll 1
-        for (int q = 0; q < ns; ++q) {
-            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q], AV = s_AV[w][q];
-            T un[NV];
-            bool neg = false;
+        for (int qb = 0; qb < ns; qb += PF) {
+            T un[PF][NV], dg[PF][NV], dh[PF][NV], fg[PF][NV], fh[PF][NV];
+            bool okq[PF];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                un[v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
-                neg = neg || !(un[v] > T(0));
-            }
-            if (first) {
-                T fg[NV], fh[NV];
-                const size_t of = (size_t)s_face[w][q] * c.Kp + k0;
-                vload(c.face + of, fg);
-                vload(c.face + FK + of, fh);
+            for (int qq = 0; qq < PF; ++qq) {
+                const int q = qb + qq;
+                okq[qq] = false;
+                if (q < ns) {
+                    const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+                    bool neg = false;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) { Fg[v] += AV * un[v] * fg[v]; Fh[v] += AV * un[v] * fh[v]; }
-            }
-            T dg[NV], dh[NV];
-            const bool ok = s_ok[w][q] && neg;
-            if (ok) {
-                const size_t oj = (size_t)s_nbr[w][q] * c.Kp + k0;
-                vload(c.dphi + oj, dg);
-                vload(c.dphi + NK + oj, dh);
+                    for (int v = 0; v < NV; ++v) {
+                        un[qq][v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
+                        neg = neg || !(un[qq][v] > T(0));
+                    }
+                    if (first) {
+                        const size_t of = (size_t)s_face[w][q] * c.Kp + k0;
+                        vload(c.face + of, fg[qq]);
+                        vload(c.face + FK + of, fh[qq]);
+                    }
+                    okq[qq] = s_ok[w][q] && neg;
+                    if (okq[qq]) {
+                        const size_t oj = (size_t)s_nbr[w][q] * c.Kp + k0;
+                        vload(c.dphi + oj, dg[qq]);
+                        vload(c.dphi + NK + oj, dh[qq]);
+                    }
+                }
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                if (un[v] > T(0)) {
-                    D[v] += AV * un[v];
-                } else if (ok) {
-                    og[v] += AV * un[v] * dg[v];
-                    oh[v] += AV * un[v] * dh[v];
+            for (int qq = 0; qq < PF; ++qq) {
+                const int q = qb + qq;
+                if (q >= ns) break;
+                const T AV = s_AV[w][q];
+                if (first) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) { Fg[v] += AV * un[qq][v] * fg[qq][v]; Fh[v] += AV * un[qq][v] * fh[qq][v]; }
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (un[qq][v] > T(0)) {
+                        D[v] += AV * un[qq][v];
+                    } else if (okq[qq]) {
+                        og[v] += AV * un[qq][v] * dg[qq][v];
+                        oh[v] += AV * un[qq][v] * dh[qq][v];
+                    }
                 }
             }
         }

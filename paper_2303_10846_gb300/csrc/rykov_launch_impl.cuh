@@ -98,7 +98,7 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
                 const int col = dir == 0 ? cc : C - 1 - cc;
                 const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
                 if (!n) continue;
-                k_macro_sweep<T><<<cdiv(n, 128), 128, 0, s>>>(d, sc.col_cell + lo, n, col,
+                k_macro_sweep<T><<<cdiv((long long)n * MACRO_LANES, 128), 128, 0, s>>>(d, sc.col_cell, lo, n, col,
                                                               it == 0 && dir == 0);
                 pf.launches += 1;
             }

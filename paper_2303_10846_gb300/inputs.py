@@ -345,6 +345,154 @@ def tet_sphere(radius: float = 0.5, box_half: float = 2.5, h_wall: float = 0.05,
                          f"tet_sphere_{int(keep.sum())}")
 
 
+# axisymmetric bodies (profile in the (x, r) half plane, nose on the axis at x = 0
+# facing -x), used for the capsule and the sphere-cone
+def _profile_segments(prof):
+    P = np.asarray(prof, dtype=np.float64)
+    return P[:-1], P[1:]
+
+
+def _axisym_sdf(prof, x, r):
+    """Signed distance (negative inside) from points (x, r) to the closed region
+    bounded by the profile polyline and the axis."""
+    A, B = _profile_segments(prof)
+    out = np.empty(len(x))
+    for s0 in range(0, len(x), 65536):
+        px, pr = x[s0:s0 + 65536, None], r[s0:s0 + 65536, None]
+        ab = B - A
+        t = ((px - A[:, 0]) * ab[:, 0] + (pr - A[:, 1]) * ab[:, 1]) / np.maximum((ab ** 2).sum(1), 1e-300)
+        t = np.clip(t, 0.0, 1.0)
+        dx = px - (A[:, 0] + t * ab[:, 0])
+        dr = pr - (A[:, 1] + t * ab[:, 1])
+        d = np.sqrt(dx * dx + dr * dr).min(axis=1)
+        # inside: crossings of a ray towards +r with the closed polygon (profile + axis)
+        Q = np.concatenate([np.asarray(prof), np.asarray(prof)[:1]], axis=0)
+        qa, qb = Q[:-1], Q[1:]
+        cross = ((qa[:, 0] <= px) & (qb[:, 0] > px)) | ((qb[:, 0] <= px) & (qa[:, 0] > px))
+        tt = (px - qa[:, 0]) / np.where(qb[:, 0] != qa[:, 0], qb[:, 0] - qa[:, 0], 1.0)
+        rc = qa[:, 1] + tt * (qb[:, 1] - qa[:, 1])
+        inside = (np.sum(cross & (rc > pr), axis=1) % 2) == 1
+        out[s0:s0 + 65536] = np.where(inside, -d, d)
+    return out
+
+
+def _resample(poly, h):
+    """Points along a polyline at arc-length spacing about h (ends included)."""
+    P = np.asarray(poly)
+    seg = np.linalg.norm(np.diff(P, axis=0), axis=1)
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    n = max(2, int(round(s[-1] / h)) + 1)
+    t = np.linspace(0.0, s[-1], n)
+    return np.stack([np.interp(t, s, P[:, 0]), np.interp(t, s, P[:, 1])], axis=1)
+
+
+def _offset_profile(prof, d):
+    """The profile moved outward by d along its vertex normals (in the (x, r) plane)."""
+    P = np.asarray(prof, dtype=np.float64)
+    t = np.gradient(P, axis=0)
+    t /= np.maximum(np.linalg.norm(t, axis=1), 1e-300)[:, None]
+    nrm = np.stack([-t[:, 1], t[:, 0]], axis=1)      # left of the direction of travel
+    Q = P + d * nrm
+    Q[:, 1] = np.maximum(Q[:, 1], 0.0)
+    return Q
+
+
+def tet_axisym_body(prof, aoa_deg: float, box_lo, box_hi, h_wall: float, growth: float,
+                    h_max: float, seed: int, name: str):
+    """Seeded Delaunay tetrahedral mesh around an axisymmetric body given by its (x, r)
+    profile (from the nose on the axis to the back on the axis, body on the left of the
+    direction of travel), turned by aoa_deg about z (flow along +x), in the box
+    [box_lo, box_hi].  Points lie on offset surfaces of the body whose spacing grows
+    geometrically from h_wall to h_max, each revolved in rings of spacing h, plus a
+    jittered lattice on the box faces.  bc 0 = body wall, bc 1 = farfield.
+    Returns (mesh, distance of every cell centre to the body)."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    prof = np.asarray(prof, dtype=np.float64)
+    box_lo, box_hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+    a = math.radians(aoa_deg)
+    Rz = np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    xc = 0.5 * (prof[:, 0].min() + prof[:, 0].max())
+    span = np.linalg.norm(box_hi - box_lo)
+    fine = _resample(prof, 0.25 * h_wall)
+    pts, d, h = [], 0.0, h_wall
+    while d < span:
+        layer = _resample(_offset_profile(fine, d) if d > 0 else fine, h)
+        for x, r in layer:
+            n = 1 if r < 0.3 * h else max(3, int(round(2.0 * math.pi * r / h)))
+            th = 2.0 * math.pi * (np.arange(n) + rng.random()) / n
+            ring = np.stack([np.full(n, x), r * np.cos(th), r * np.sin(th)], axis=1)
+            if d > 0:
+                ring += 0.1 * h * (rng.random((n, 3)) - 0.5)
+            pts.append(ring)
+        d += 0.82 * h
+        h = min(h * growth, h_max)
+    P = np.concatenate(pts, axis=0)
+    body = P.copy()
+    P = (P - [xc, 0.0, 0.0]) @ Rz.T + [xc, 0.0, 0.0]
+    sd = _axisym_sdf(prof, body[:, 0], np.hypot(body[:, 1], body[:, 2]))
+    ok = np.all((P > box_lo + 0.3 * h_max) & (P < box_hi - 0.3 * h_max), axis=1)
+    ok &= (sd > -1e-9) & ((sd > 0.3 * h_wall) | (np.abs(sd) < 1e-9))
+    pts = [P[ok]]
+    for dd in range(3):
+        m = int(math.ceil((box_hi[dd] - box_lo[dd]) / h_max))
+        od = [x for x in range(3) if x != dd]
+        ga = np.linspace(box_lo[od[0]], box_hi[od[0]], int(math.ceil((box_hi[od[0]] - box_lo[od[0]]) / h_max)) + 1)
+        gb = np.linspace(box_lo[od[1]], box_hi[od[1]], int(math.ceil((box_hi[od[1]] - box_lo[od[1]]) / h_max)) + 1)
+        A_, B_ = np.meshgrid(ga, gb, indexing="ij")
+        A_, B_ = A_.ravel(), B_.ravel()
+        inner = ((A_ > box_lo[od[0]] + 1e-12) & (A_ < box_hi[od[0]] - 1e-12) &
+                 (B_ > box_lo[od[1]] + 1e-12) & (B_ < box_hi[od[1]] - 1e-12))
+        for sv in (box_lo[dd], box_hi[dd]):
+            q = np.zeros((A_.size, 3))
+            q[:, dd] = sv
+            q[:, od[0]] = A_ + inner * 0.2 * h_max * (rng.random(A_.size) - 0.5)
+            q[:, od[1]] = B_ + inner * 0.2 * h_max * (rng.random(B_.size) - 0.5)
+            pts.append(q)
+    pts = np.unique(np.round(np.concatenate(pts, axis=0), 12), axis=0)
+    tri = Delaunay(pts)
+    tets = tri.simplices.astype(np.int64)
+    Pt = pts[tets]
+    cen = Pt.mean(axis=1)
+    vol = np.abs(np.einsum("ij,ij->i", Pt[:, 1] - Pt[:, 0],
+                           np.cross(Pt[:, 2] - Pt[:, 0], Pt[:, 3] - Pt[:, 0]))) / 6.0
+    back = (cen - [xc, 0.0, 0.0]) @ Rz + [xc, 0.0, 0.0]        # into the body frame
+    sdc = _axisym_sdf(prof, back[:, 0], np.hypot(back[:, 1], back[:, 2]))
+    keep = (sdc > 0.0) & (vol > 1e-14)
+
+    def wall_test(c):
+        b = (c - [xc, 0.0, 0.0]) @ Rz + [xc, 0.0, 0.0]
+        return _axisym_sdf(prof, np.array([b[0]]), np.array([math.hypot(b[1], b[2])]))[0] < 0.25 * h_wall
+
+    mesh = _tets_to_mesh(pts, tets, keep, wall_test, f"{name}_{int(keep.sum())}")
+    bc = (mesh.cell_center - [xc, 0.0, 0.0]) @ Rz + [xc, 0.0, 0.0]
+    dist = _axisym_sdf(prof, bc[:, 0], np.hypot(bc[:, 1], bc[:, 2]))
+    return mesh, dist
+
+
+def capsule_profile(R_n: float = 1.0, r_max: float = 0.8, cone_deg: float = 33.0, r_back: float = 0.3,
+                    n_arc: int = 64):
+    """Blunt capsule: spherical-cap heat shield of radius R_n up to the shoulder radius
+    r_max, conical afterbody closing at cone_deg to r_back, flat back."""
+    th_c = math.asin(r_max / R_n)
+    th = np.linspace(0.0, th_c, n_arc)
+    cap = np.stack([R_n * (1.0 - np.cos(th)), R_n * np.sin(th)], axis=1)
+    xs = cap[-1, 0]
+    xb = xs + (r_max - r_back) / math.tan(math.radians(cone_deg))
+    return np.concatenate([cap, [[xb, r_back], [xb, 0.0]]], axis=0)
+
+
+def sphere_cone_profile(R_n: float = 1.0, half_deg: float = 15.0, length: float = 4.0, n_arc: int = 64):
+    """Sphere-cone: nose of radius R_n, tangent cone of half angle half_deg up to x =
+    length, flat base."""
+    tc = math.radians(90.0 - half_deg)
+    th = np.linspace(0.0, tc, n_arc)
+    nose = np.stack([R_n * (1.0 - np.cos(th)), R_n * np.sin(th)], axis=1)
+    xt, rt = nose[-1]
+    rb = rt + (length - xt) * math.tan(math.radians(half_deg))
+    return np.concatenate([nose, [[length, rb], [length, 0.0]]], axis=0)
+
+
 # ----------------------------------------------------------------------------------
 # discrete velocity spaces
 # ----------------------------------------------------------------------------------
@@ -504,3 +652,54 @@ def sphere_workload(h_wall: float = 0.065, growth: float = 1.15, h_max: float = 
                     dvs=dvs, params=params, bcs=bcs, prim0=prim,
                     ref=dict(rho=1.0, U=U, T=1.0),
                     meta=dict(ma=ma, kn=kn, T_w=T_w))
+
+
+def capsule_workload(h_wall: float = 0.047, growth: float = 1.12, h_max: float = 0.39,
+                     dvs_target: int = 6000, ma: float = 10.0, kn: float = 0.01,
+                     aoa: float = 25.0, T_w: float = 300.0 / 142.0, Z_rot: float = 3.5,
+                     cfl_imp: float = 1000.0, mesh_seed: int = 20263,
+                     dvs_seed: int = 20264) -> Workload:
+    """Blunt capsule (spherical-cap heat shield R = 1 up to the shoulder radius 0.8,
+    33-degree conical afterbody to radius 0.3, flat back) at 25 degrees angle of
+    attack, Mach 10 along +x, Kn on the maximum diameter (1.6), T_w = 300/142 T_inf,
+    in the box [-3.2, 4.8] x [-4, 4]^2; near-continuum DVS (outer radius 5 sqrt(R T0))."""
+    prof = capsule_profile()
+    D = 1.6
+    mesh, dist = tet_axisym_body(prof, aoa, [-3.2, -4.0, -4.0], [4.8, 4.0, 4.0], h_wall, growth,
+                                 h_max, mesh_seed, "tet_capsule")
+    a = math.sqrt(1.4 * R_GAS)
+    U = (ma * a, 0.0, 0.0)
+    dvs = unstructured_dvs(U, 1.0, T_w, ma, transitional=(kn >= 0.1), target=dvs_target,
+                           seed=dvs_seed)
+    params = Params(Z_rot=Z_rot, mu_ref=mu_ref_from_kn(kn, 0.74, length=D), cfl_imp=cfl_imp,
+                    cfl_imp0=2.0, cfl_ramp=1.3, first_order_iters=10)
+    bcs = [BC(BC_WALL, 1.0, (0.0, 0.0, 0.0), T_w), BC(BC_FARFIELD, 1.0, U, 1.0)]
+    prim = uniform_prim(mesh.n_cell, 1.0, U, 1.0)
+    prim[:, 1:4] *= np.clip(dist / D, 0.0, 1.0)[:, None]
+    return Workload(name=f"capsule_ma{ma:g}_kn{kn:g}_aoa{aoa:g}_N{mesh.n_cell}_K{dvs.K}", mesh=mesh,
+                    dvs=dvs, params=params, bcs=bcs, prim0=prim, ref=dict(rho=1.0, U=U, T=1.0),
+                    meta=dict(ma=ma, kn=kn, aoa=aoa, T_w=T_w, length=D, profile=prof.tolist()))
+
+
+def cone_scale_workload(h_wall: float = 0.065, growth: float = 1.12, h_max: float = 0.45,
+                        dvs_target: int = 8000, ma: float = 8.0, kn: float = 0.005,
+                        T_w: float = 1.0, Z_rot: float = 3.5, cfl_imp: float = 1000.0,
+                        mesh_seed: int = 20265, dvs_seed: int = 20266) -> Workload:
+    """Scale case: sphere-cone (nose radius 1, 15-degree half angle, length 4, flat
+    base) at zero incidence, Mach 8, Kn on the nose radius, T_w = T_inf (the case gives
+    none), in the box [-4, 10] x [-5, 5]^2: ~500k tetrahedra x ~8,000 velocities."""
+    prof = sphere_cone_profile()
+    mesh, dist = tet_axisym_body(prof, 0.0, [-4.0, -5.0, -5.0], [10.0, 5.0, 5.0], h_wall, growth,
+                                 h_max, mesh_seed, "tet_cone")
+    a = math.sqrt(1.4 * R_GAS)
+    U = (ma * a, 0.0, 0.0)
+    dvs = unstructured_dvs(U, 1.0, T_w, ma, transitional=(kn >= 0.1), target=dvs_target,
+                           seed=dvs_seed)
+    params = Params(Z_rot=Z_rot, mu_ref=mu_ref_from_kn(kn, 0.74, length=1.0), cfl_imp=cfl_imp,
+                    cfl_imp0=2.0, cfl_ramp=1.3, first_order_iters=10)
+    bcs = [BC(BC_WALL, 1.0, (0.0, 0.0, 0.0), T_w), BC(BC_FARFIELD, 1.0, U, 1.0)]
+    prim = uniform_prim(mesh.n_cell, 1.0, U, 1.0)
+    prim[:, 1:4] *= np.clip(dist / 1.0, 0.0, 1.0)[:, None]
+    return Workload(name=f"cone_ma{ma:g}_kn{kn:g}_N{mesh.n_cell}_K{dvs.K}", mesh=mesh, dvs=dvs,
+                    params=params, bcs=bcs, prim0=prim, ref=dict(rho=1.0, U=U, T=1.0),
+                    meta=dict(ma=ma, kn=kn, T_w=T_w, length=1.0, profile=prof.tolist()))

@@ -32,7 +32,7 @@ EXPORTS = ["rk_version", "rk_create", "rk_destroy", "rk_last_error", "rk_upload_
            "rk_debug_get", "rk_profile", "rk_profile_get", "rk_residual_noalloc",
            "rk_noalloc_last_error", "rk_state_len", "rk_adjoint_workspace_size",
            "rk_bind_adjoint_workspace", "rk_get_state", "rk_put_state", "rk_steady_residual",
-           "rk_vjp", "rk_objective", "rk_adjoint_solve", "rk_adjoint_get"]
+           "rk_vjp", "rk_objective", "rk_adjoint_solve", "rk_adjoint_get", "rk_debug_rows"]
 RK_OBJ_HEAT, RK_OBJ_DRAG = 0, 1
 OBJECTIVES = {"heat": RK_OBJ_HEAT, "drag": RK_OBJ_DRAG}
 PROF_CLASSES = ["recon", "face_interior", "face_boundary", "fluxes", "macro_sgs",
@@ -96,6 +96,7 @@ def load(path: str | None = None):
         "rk_objective": ([vp, C.c_int, vp, vp, vp, C.c_int], C.c_int),
         "rk_adjoint_solve": ([vp, C.c_int, i32, dp, P(i32), vp, vp, vp], C.c_int),
         "rk_adjoint_get": ([vp, vp, C.c_int], C.c_int),
+        "rk_debug_rows": ([vp, C.c_int, vp, i64, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -236,6 +237,13 @@ class Solver:
         out = np.empty(int(np.prod(shp)))
         self._check(self.L.rk_debug_get(self.h, BUF[name], _ptr(out), out.size))
         return out.reshape(shp)
+
+    def debug_rows(self, name: str, rows):
+        """rows of PHI / RES / DPHI / MICRO_F (cells) or FACE (faces): [2, n, K]."""
+        rows = _c(rows, np.int64)
+        out = np.empty((2, len(rows), self.K))
+        self._check(self.L.rk_debug_rows(self.h, BUF[name], _ptr(rows), len(rows), _ptr(out)))
+        return out
 
     def moments(self):
         W = np.empty((self.N, 6)); q = np.empty((self.N, 6)); T3 = np.empty((self.N, 3))

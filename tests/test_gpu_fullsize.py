@@ -1,0 +1,157 @@
+"""Parity at the benchmark's full size: the Ma-5 sphere, N = 61,911 tetrahedra, K = 3,033
+velocities, iterated in the benchmark's launch configuration (the CUDA graph of one
+iteration), FP64 and mixed precision.  The oracle cannot run the whole case in a test,
+so it checks sampled outputs one at a time (interface kernel per face from the GPU's
+own inputs, micro residual per cell) and the tests check properties that hold at any
+size (mixed vs FP64 surface quantities, bitwise repeatability).
+
+Tolerances: FP64 1e-10 relative to the scale of the summed terms (the micro flux and
+the residual are small differences of large terms).  Mixed: 2e-5,
+because the GPU works in FP32 (relative rounding 6e-8, interface state from
+float-float moments), while the oracle is fed the FP32 values widened to FP64.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_10846_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    return I.sphere_workload()
+
+
+def _solver(wl, prec, debug=False):
+    from paper_2303_10846_gb300.rykov import Solver
+    return Solver(wl, prec, debug=debug)
+
+
+TOLS = {"fp64": 1e-10, "mixed": 2e-5}
+
+
+def check_sampled(s, wl, prec, n_iter, debug, n_faces=48, n_cells=48, seed=2024):
+    """Iterate n_iter times (graph path), then step through one more iteration and
+    check sampled interior faces (interface kernel from the GPU's own phi(x_f - u s))
+    and sampled cells (micro flux by its definition from the face values, first-sweep
+    residual with the oracle's equilibrium at (W~, q^n))."""
+    from paper_2303_10846_gb300 import rykov as RK
+    m = wl.mesh
+    tol = TOLS[prec]
+    s.iterate(n_iter)
+    rng = np.random.default_rng(seed)
+    interior = np.nonzero(m.face_cell[:, 1] >= 0)[0]
+    faces = np.sort(rng.choice(interior, n_faces, replace=False))
+    cells = np.sort(rng.choice(m.n_cell, n_cells, replace=False))
+    s.step(RK.STEP_RECON)
+    phi0 = s.debug_rows("FACE", faces)
+    s.step(RK.STEP_FACES)
+    phif = s.debug_rows("FACE", faces)
+    fst = s.debug_get("FSTATE") if debug else None
+    sf = s.debug_get("S")
+    u, w = wl.dvs.u, wl.dvs.w
+    for j, f in enumerate(faces):
+        st, gf, hf = O.interface(wl.params, u, w, phi0[0, j], phi0[1, j], sf[f])
+        sc = max(np.max(np.abs(gf)), np.max(np.abs(hf)))
+        assert np.max(np.abs(phif[0, j] - gf)) <= tol * sc, f"face {f} g"
+        assert np.max(np.abs(phif[1, j] - hf)) <= tol * sc, f"face {f} h"
+        if fst is not None:
+            for idx in (0, 4, 5, 6, 7):             # rho, T, T_tr, T_rot, tau
+                assert abs(fst[f, idx] - st[idx]) <= tol * abs(st[idx]), f"face {f} state {idx}"
+            qs = max(np.max(np.abs(st[8:14])), 1e-300)
+            assert np.max(np.abs(fst[f, 8:14] - st[8:14])) <= 10 * tol * qs + 1e-14, f"face {f} q"
+    s.step(RK.STEP_FLUXES)
+    phi = s.debug_rows("PHI", cells)
+    q_n = s.debug_get("Q")
+    # the micro flux is a small difference of large face terms: errors are measured on
+    # the scale of the terms (sum of their magnitudes), as for any cancelling sum
+    Fd = np.zeros((2, len(cells), wl.dvs.K))
+    Fs = np.zeros(len(cells))
+    for j, i in enumerate(cells):
+        fl = np.nonzero((m.face_cell[:, 0] == i) | (m.face_cell[:, 1] == i))[0]
+        vals = s.debug_rows("FACE", fl)
+        mag = np.zeros((2, wl.dvs.K))
+        for t, f in enumerate(fl):
+            sg = 1.0 if m.face_cell[f, 0] == i else -1.0
+            term = m.face_area[f] * sg * (u @ m.face_normal[f]) * vals[:, t] / m.cell_volume[i]
+            Fd[:, j] += term
+            mag += np.abs(term)
+        Fs[j] = np.max(mag)
+    if debug:
+        F = s.debug_rows("MICRO_F", cells)
+        for j, i in enumerate(cells):
+            assert np.max(np.abs(F[:, j] - Fd[:, j])) <= tol * Fs[j], f"cell {i} flux"
+    s.step(RK.STEP_MACRO)
+    Wt = s.debug_get("WT")
+    taut = s.debug_get("TAUT")
+    s.step(RK.STEP_MICRO)
+    res = s.debug_rows("RES", cells)
+    R = wl.params.R
+    for j, i in enumerate(cells):
+        W = Wt[i]
+        rho = W[0]
+        U = W[1:4] / rho
+        ke = 0.5 * rho * U @ U
+        T = (W[4] - ke) / (2.5 * rho * R)
+        Trot = W[5] / (rho * R)
+        Ttr = (W[4] - ke - W[5]) / (1.5 * rho * R)
+        stt = O.make_state(rho, U, T, Ttr, Trot, q_n[i, :3], q_n[i, 3:])
+        G, H = O.equilibrium(wl.params, stt, u)
+        coll = np.stack([(G - phi[0, j]) / taut[i], (H - phi[1, j]) / taut[i]])
+        sc = max(np.max(np.abs(phi[:, j])) / taut[i], Fs[j])
+        assert np.max(np.abs(res[:, j] - (coll - Fd[:, j]))) <= tol * sc, f"cell {i} residual"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sampled_faces_and_cells_at_full_size(sphere, prec):
+    """Sphere, the bench workload, past the first-order start."""
+    s = _solver(sphere, prec, debug=True)
+    check_sampled(s, sphere, prec, 12, True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_capsule_sampled(prec):
+    """Capsule at 25 degrees angle of attack, Mach 10, Kn 0.01: ~205k tetrahedra x ~6,000
+    velocities (the capsule configuration, checked at its full size)."""
+    wl = I.capsule_workload()
+    s = _solver(wl, prec, debug=(prec == "mixed"))
+    check_sampled(s, wl, prec, 12, prec == "mixed", n_faces=32, n_cells=32)
+
+
+def test_scale_case_sampled():
+    """Scale case: sphere-cone, ~520k tetrahedra x ~7,900 velocities in mixed precision
+    (about 190 GB of device arrays), one second-order iteration checked on samples."""
+    wl = I.cone_scale_workload()
+    wl.params.first_order_iters = 0
+    s = _solver(wl, "mixed", debug=False)
+    check_sampled(s, wl, "mixed", 1, False, n_faces=24, n_cells=24)
+
+
+def test_mixed_matches_fp64_on_the_surface_at_full_size(sphere):
+    """North-star accuracy target of the mixed form: wall pressure, heat flux and drag
+    within 1e-5 (relative to their largest values) of the FP64 form after the same
+    iterations from the same state."""
+    s64 = _solver(sphere, "fp64")
+    s32 = _solver(sphere, "mixed")
+    s64.iterate(40)
+    s32.iterate(40)
+    p64, f64, h64 = s64.surface()
+    p32, f32, h32 = s32.surface()
+    assert np.max(np.abs(p32[:, 0] - p64[:, 0])) <= 1e-5 * np.max(np.abs(p64[:, 0]))     # p_w
+    assert np.max(np.abs(p32[:, 4] - p64[:, 4])) <= 1e-5 * np.max(np.abs(p64[:, 4]))     # q_w
+    e = np.asarray(sphere.ref["U"]) / np.linalg.norm(sphere.ref["U"])
+    assert abs(f32 @ e - f64 @ e) <= 1e-5 * abs(f64 @ e)                                 # drag
+    assert abs(h32 - h64) <= 1e-5 * np.max(np.abs(p64[:, 4])) * np.sum(sphere.mesh.face_area[
+        np.nonzero(sphere.mesh.face_cell[:, 1] == -1)[0]])
+
+
+def test_full_size_iterations_are_bitwise_repeatable(sphere):
+    s = _solver(sphere, "mixed")
+    s.iterate(25)
+    W1, q1, _ = s.moments()
+    s.set_state_prim(sphere.prim0)
+    s.iterate(25)
+    W2, q2, _ = s.moments()
+    assert np.array_equal(W1, W2) and np.array_equal(q1, q2)

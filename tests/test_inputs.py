@@ -65,3 +65,60 @@ def test_unstructured_dvs_criterion():
     assert np.all(np.linalg.norm(d.u - 0.4 * np.array(U), axis=1) < r)
     n_ball = (np.linalg.norm(d.u - np.array(U), axis=1) < 3 * math.sqrt(0.5)).sum()
     assert abs(n_ball - I.refined_ball_cells(1.0)) < 60         # Eq. solve_weight: 730
+
+
+def _axisym_volume(prof):
+    """Volume of revolution of a closed (x, r) profile (Pappus: 2 pi * area * centroid r)."""
+    P = np.asarray(prof)
+    P = np.concatenate([P, P[:1]])
+    x, r = P[:, 0], P[:, 1]
+    cross = x[:-1] * r[1:] - x[1:] * r[:-1]
+    area = 0.5 * cross.sum()
+    rc = ((r[:-1] + r[1:]) * cross).sum() / (6.0 * area)
+    return abs(2.0 * math.pi * area * rc)
+
+
+@pytest.mark.parametrize("which", ["capsule", "cone"])
+def test_axisymmetric_body_meshes(which):
+    """Closed, positive, properly coloured; the meshed volume is the box minus the body
+    (inscribed faceting: small deficit); wall faces lie on the body."""
+    if which == "capsule":
+        prof = I.capsule_profile()
+        lo, hi, aoa = np.array([-3.2, -4, -4]), np.array([4.8, 4, 4]), 25.0
+    else:
+        prof = I.sphere_cone_profile()
+        lo, hi, aoa = np.array([-4, -5, -5]), np.array([10, 5, 5]), 0.0
+    m, dist = I.tet_axisym_body(prof, aoa, lo, hi, 0.15, 1.3, 0.8, 7, which)
+    assert _closure(m) < 1e-12
+    assert np.all(m.cell_volume > 0) and np.all(dist > 0)
+    box = np.prod(hi - lo)
+    body = _axisym_volume(prof)
+    # the body is replaced by a faceted hole; the volume error is about surface area x
+    # a fraction of the wall spacing
+    area = 2 * math.pi * np.sum(0.5 * (prof[1:, 1] + prof[:-1, 1]) * np.hypot(*np.diff(prof, axis=0).T))
+    assert abs(m.cell_volume.sum() - (box - body)) < 0.2 * area * 0.15
+    fc = m.face_cell
+    it = fc[:, 1] >= 0
+    assert np.all(m.cell_colour[fc[it, 0]] != m.cell_colour[fc[it, 1]])
+    wall = fc[:, 1] == -1
+    assert wall.sum() > 100 and (fc[:, 1] == -2).sum() > 100
+    # wall face centres are on the body surface (within the faceting sag)
+    xc = 0.5 * (prof[:, 0].min() + prof[:, 0].max())
+    a = math.radians(aoa)
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    b = (m.face_center[wall] - [xc, 0, 0]) @ Rz + [xc, 0, 0]
+    sd = I._axisym_sdf(prof, b[:, 0], np.hypot(b[:, 1], b[:, 2]))
+    assert np.max(np.abs(sd)) < 0.05
+
+
+def test_capsule_and_scale_workload_sizes():
+    """The capsule configuration: ~200k tetrahedra x ~6,000 velocities (Mach 10, 25
+    degrees); the scale DVS: ~8,000 velocities (the mesh is built on the GPU runs)."""
+    wl = I.capsule_workload()
+    assert 190_000 < wl.mesh.n_cell < 220_000 and 5_500 < wl.dvs.K < 6_500
+    assert wl.bcs[0].T == pytest.approx(300.0 / 142.0)
+    U = np.asarray(wl.bcs[1].U)
+    assert np.linalg.norm(U) == pytest.approx(10.0 * math.sqrt(1.4 * I.R_GAS))
+    a = math.sqrt(1.4 * I.R_GAS)
+    d = I.unstructured_dvs((8 * a, 0, 0), 1.0, 1.0, 8.0, transitional=False, target=8000, seed=20266)
+    assert 7_500 < d.K < 8_500
