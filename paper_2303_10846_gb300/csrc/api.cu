@@ -56,6 +56,9 @@ extern "C" int rk_destroy(rk_ctx* ctx) {
     for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
     return RK_OK;
 }
@@ -506,7 +509,10 @@ static cudaError_t launch_step(rk_ctx* ctx, rk::Dev<T>& d, int step, cudaStream_
     switch (step) {
         case RK_STEP_RECON: return rk::Launch<T>::recon(d, s, ctx->prof);
         case RK_STEP_FACES: return rk::Launch<T>::faces(d, s, ctx->prof);
-        case RK_STEP_FLUXES: return rk::Launch<T>::fluxes(d, s, ctx->prof);
+        case RK_STEP_FLUXES: {
+            cudaError_t e = rk::Launch<T>::fluxes(d, s, ctx->prof);
+            return e != cudaSuccess ? e : rk::Launch<T>::micro_flux(d, s, ctx->prof);
+        }
         case RK_STEP_MACRO: return rk::Launch<T>::macro(d, s, ctx->sched, ctx->p.n_macro_sgs, ctx->prof);
         case RK_STEP_MICRO: return rk::Launch<T>::micro(d, s, ctx->sched, ctx->p.n_micro_sgs, ctx->prof);
         default: return cudaErrorInvalidValue;
@@ -531,9 +537,23 @@ static int build_graph(rk_ctx* ctx, rk::Dev<T>& d) {
     const long long l0 = ctx->prof.launches;
     ctx->prof.on = false;
     cudaGraph_t g = nullptr;
+    if (!ctx->cap2) CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
+    if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int st = RK_STEP_RECON; st <= RK_STEP_MICRO && e == cudaSuccess; ++st) e = launch_step(ctx, d, st, ctx->cap);
+    // reconstruction and faces; then two branches: the micro flux gather on a second
+    // stream while the macro fluxes and the macro PR-SGS (latency-bound, few SMs busy)
+    // run on the first; joined before the micro sweeps
+    cudaError_t e = launch_step(ctx, d, RK_STEP_RECON, ctx->cap);
+    if (e == cudaSuccess) e = launch_step(ctx, d, RK_STEP_FACES, ctx->cap);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap2, ctx->ev_fork, 0);
+    if (e == cudaSuccess) e = rk::Launch<T>::micro_flux(d, ctx->cap2, ctx->prof);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->cap2);
+    if (e == cudaSuccess) e = rk::Launch<T>::fluxes(d, ctx->cap, ctx->prof);
+    if (e == cudaSuccess) e = launch_step(ctx, d, RK_STEP_MACRO, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
+    if (e == cudaSuccess) e = launch_step(ctx, d, RK_STEP_MICRO, ctx->cap);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
     ctx->graph_kernels = ctx->prof.launches - l0;
     ctx->prof.launches = l0;

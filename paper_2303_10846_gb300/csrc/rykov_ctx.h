@@ -77,7 +77,8 @@ struct rk_ctx {
     // the caller's stream); rebuilt after anything baked into it changes
     bool use_graph = true;
     bool use_coop = false;            // cooperative launch of the macro PR-SGS (RYKOV_COOP=1)
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;   // capture streams (main, side branch)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long graph_kernels = 0;
     double last_res[6] = {0, 0, 0, 0, 0, 0};

@@ -28,6 +28,9 @@ constexpr int MAXF = 8;        // faces per cell
 #ifndef MICRO_FIRST_MINB
 #define MICRO_FIRST_MINB 3
 #endif
+#ifndef MICRO_FIRST_NV
+#define MICRO_FIRST_NV 4
+#endif
 #ifndef MICRO_MID_MINB
 #define MICRO_MID_MINB 4
 #endif
@@ -1211,6 +1214,58 @@ __global__ void k_macro_finish(Dev<T> c) {
     e[24] = 1.0 / (cfl * c.dt[i]) + 1.0 / tau;
 }
 
+// Micro flux F_{i,k} = sum_j (A/V_i)(u_k . n_ij) phi_ij,k (Eq. implicit_mic_flux) of
+// every cell, gathered from the face array into res (the first micro sweep turns it
+// into the residual in place).  It needs only the face distributions, so it runs
+// while the macro PR-SGS (which it does not touch) solves on another stream.  One warp
+// per cell, faces in slot order.
+template <typename T, int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_micro_flux(Dev<T> c) {
+    constexpr int NV = VW<T>::N;
+    __shared__ int s_face[WPB][MAXF];
+    __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * WPB + w;
+    if (i >= c.N) return;
+    const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
+    if (lane < ns) {
+        const int m = s0 + lane;
+        s_face[w][lane] = c.slot_face[m];
+        const T sg = c.slot_left[m] ? T(1) : T(-1);
+        s_n[w][0][lane] = sg * c.slot_nT[m];
+        s_n[w][1][lane] = sg * c.slot_nT[c.nnz + m];
+        s_n[w][2][lane] = sg * c.slot_nT[2 * c.nnz + m];
+        s_AV[w][lane] = c.slot_AVT[m];
+    }
+    __syncwarp();
+    const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
+    const size_t oi = (size_t)i * c.Kp;
+    for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+        T ux[NV], uy[NV], uz[NV], Fg[NV], Fh[NV];
+        vload(c.uT + k0, ux);
+        vload(c.uT + c.Kp + k0, uy);
+        vload(c.uT + 2 * c.Kp + k0, uz);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fg[v] = Fh[v] = T(0);
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q], AV = s_AV[w][q];
+            T fg[NV], fh[NV];
+            const size_t of = (size_t)s_face[w][q] * c.Kp + k0;
+            vload(c.face + of, fg);
+            vload(c.face + FK + of, fh);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const T un = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
+                Fg[v] += AV * un * fg[v];
+                Fh[v] += AV * un * fh[v];
+            }
+        }
+        vstore(c.res + oi + k0, Fg);
+        vstore(c.res + NK + oi + k0, Fh);
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Step 5 (micro PR-SGS, Eq. implicit_mic_final_equ) and Step 6 (update and integral
 // error compensation, Eqs. solve_rho - solve_qrot).  One block per cell of one
@@ -1230,7 +1285,7 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
     constexpr bool first = FIRST, last = LAST, first_forward = FIRST;
     using R = Red<T>;
     // velocities per lane: 16-byte accesses in the middle sweeps of the mixed mode
-    constexpr int NV = (sizeof(T) == 4 && !FIRST && !LAST) ? MICRO_MID_NV : VW<T>::N;
+    constexpr int NV = sizeof(T) == 8 ? 1 : (FIRST ? MICRO_FIRST_NV : (LAST ? 2 : MICRO_MID_NV));
     // faces whose loads are issued together
     constexpr int PF = MICRO_PF;
     __shared__ T s_e[WPB][EQN + 2];
@@ -1272,7 +1327,7 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
         // over the faces is unchanged)
 #pragma unroll 1
         for (int qb = 0; qb < ns; qb += PF) {
-            T un[PF][NV], dg[PF][NV], dh[PF][NV], fg[PF][NV], fh[PF][NV];
+            T un[PF][NV], dg[PF][NV], dh[PF][NV];
             bool okq[PF];
 #pragma unroll
             for (int qq = 0; qq < PF; ++qq) {
@@ -1285,11 +1340,6 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
                     for (int v = 0; v < NV; ++v) {
                         un[qq][v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
                         neg = neg || !(un[qq][v] > T(0));
-                    }
-                    if (first) {
-                        const size_t of = (size_t)s_face[w][q] * c.Kp + k0;
-                        vload(c.face + of, fg[qq]);
-                        vload(c.face + FK + of, fh[qq]);
                     }
                     okq[qq] = s_ok[w][q] && neg;
                     if (okq[qq]) {
@@ -1304,10 +1354,6 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
                 const int q = qb + qq;
                 if (q >= ns) break;
                 const T AV = s_AV[w][q];
-                if (first) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) { Fg[v] += AV * un[qq][v] * fg[qq][v]; Fh[v] += AV * un[qq][v] * fh[qq][v]; }
-                }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (un[qq][v] > T(0)) {
@@ -1331,6 +1377,9 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
             vload(c.phi + NK + oi + k0, ph);
         }
         if (first) {
+            // res holds the micro flux F (k_micro_flux); Res replaces it in place
+            vload(c.res + oi + k0, Fg);
+            vload(c.res + NK + oi + k0, Fh);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 rg[v] = (G[v] - pg[v]) * itau - Fg[v];

@@ -47,6 +47,8 @@ struct Launch {
     static cudaError_t recon(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t faces(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf);
+    // micro flux F into res: independent of the macro solve (a parallel graph branch)
+    static cudaError_t micro_flux(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
                              Prof& pf);
     static cudaError_t micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,

@@ -66,6 +66,15 @@ cudaError_t Launch<T>::fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf) {
 }
 
 template <typename T>
+cudaError_t Launch<T>::micro_flux(const Dev<T>& d, cudaStream_t s, Prof& pf) {
+    pf.begin(3, s);
+    k_micro_flux<T, MICRO_WPB><<<cdiv(d.N, MICRO_WPB), MICRO_WPB * 32, 0, s>>>(d);
+    pf.end(s);
+    pf.launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
                              Prof& pf) {
     pf.begin(4, s);
@@ -125,12 +134,10 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             // sweep applies the update and the Step-6 sums
             pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
             const dim3 g(cdiv(n, MICRO_WPB)), b(MICRO_WPB * 32);
-            if (sw == 0)
-                k_micro_sweep<T, MICRO_WPB, true, false><<<g, b, 0, s>>>(d, sc.col_cell + lo, n, col);
-            else if (sw == nsw - 1)
-                k_micro_sweep<T, MICRO_WPB, false, true><<<g, b, 0, s>>>(d, sc.col_cell + lo, n, col);
-            else
-                k_micro_sweep<T, MICRO_WPB, false, false><<<g, b, 0, s>>>(d, sc.col_cell + lo, n, col);
+            const int* cl = sc.col_cell + lo;
+            if (sw == 0) k_micro_sweep<T, MICRO_WPB, true, false><<<g, b, 0, s>>>(d, cl, n, col);
+            else if (sw == nsw - 1) k_micro_sweep<T, MICRO_WPB, false, true><<<g, b, 0, s>>>(d, cl, n, col);
+            else k_micro_sweep<T, MICRO_WPB, false, false><<<g, b, 0, s>>>(d, cl, n, col);
             pf.end(s);
             pf.launches += 1;
         }
