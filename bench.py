@@ -37,7 +37,7 @@ START_ITERS = 10          # start-up iterations (first order, CFL ramp), untimed
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
 # as they stand, mixed precision, full sphere workload: one ncu capture on the same mesh
 # with every 5th velocity (K = 607), scaled by 3033/607 (traffic is proportional to K)
-NCU_TRAFFIC_MIXED = {"k_micro_sweep": 1.598e9, "k_recon": 4.700e9, "k_face_interior": 5.667e9}
+NCU_TRAFFIC_MIXED = {"k_recon": 4.707e9, "k_face_interior": 5.667e9}
 
 
 def _peaks():
@@ -298,8 +298,8 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0:
         peak, peak_kind = _peaks()
         Tsz = 4 if args.precision == "mixed" else 8
-        # dominant kernel class and its roofline (algorithmic bytes per launch, see
-        # the design doc for the per-unit figures)
+        # dominant kernel class and its roofline (algorithmic bytes per launch from the
+        # per-unit word counts below)
         F, Fi = wl.mesh.n_face, int((wl.mesh.face_cell[:, 1] >= 0).sum())
         nnz = 2 * Fi + (F - Fi)
         # kernels (the micro sweep's first / middle / last launches are one kernel)
@@ -310,10 +310,13 @@ def run_gpu(args, rank, world, local_rank):
                                                 prof["micro_sweep_last"]))),
         }
         nsw = 2 * 2                                     # 2 x (forward + backward)
-        # algorithmic words per unit per step: micro 16 + 6 (nsw - 2) + 12
-        # per (cell, k); recon 2 per (cell, k) + 2 per (face, k); faces 4 per (face, k)
+        # algorithmic words per unit per step (each input element read once, each output
+        # written once): micro sweeps 10 (first: phi, F, neighbour dphi; Res, dphi) +
+        # 6 per middle sweep (Res, neighbour dphi; dphi) + 10 (last: Res, neighbour dphi,
+        # phi; phi, dphi) per (cell, k); recon 2 per (cell, k) + 2 per (face, k); faces 4
+        # per (face, k)
         algo_step = {
-            "k_micro_sweep": (16 + 6 * (nsw - 2) + 12) * N * K * Tsz,
+            "k_micro_sweep": (10 + 6 * (nsw - 2) + 10) * N * K * Tsz,
             "k_recon": (2 * N * K + 2 * F * K) * Tsz,
             "k_face_interior": 4 * Fi * K * Tsz,
         }

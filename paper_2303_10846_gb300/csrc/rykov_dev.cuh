@@ -1142,45 +1142,53 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The wait is
-// bounded: after one second without the barrier opening the block records status
-// bit 4 and stops waiting (every other block then stops at its next wait), so a
-// failure returns RK_ETIMEOUT to the host instead of hanging the GPU.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status) {
+// Grid-wide barrier of a cooperative launch (all blocks co-resident): a counter that
+// only grows within one macro solve (k_macro_prep zeroes it); barrier number nb is
+// passed when it reaches (nb + 1) blocks x grid.  The wait is bounded: thread 0 reads
+// the clock every 1024 polls and after one second without the barrier opening records
+// status bit 4 and stops waiting, so a failure returns RK_ETIMEOUT to the host instead
+// of hanging the GPU (every other block then gives up at its own next wait).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int& nb) {
+    __shared__ int s_fail;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* gen = bar + 1;
-        const unsigned int g = *gen;
+        const unsigned int target = (nb + 1u) * gridDim.x;
+        int fail = 0;
         __threadfence();
-        const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*gen == g) {
-                if ((*(volatile int*)status & 4) || global_ns() - t0 > 1000000000ull) {
+        atomicAdd(bar, 1u);
+        unsigned int polls = 0;
+        unsigned long long t0 = 0;
+        while (ld_acquire_gpu(bar) < target) {
+            if ((++polls & 1023u) == 0u) {
+                const unsigned long long t = global_ns();
+                if (t0 == 0) t0 = t;
+                else if (t - t0 > 1000000000ull || (*(volatile int*)status & 4)) {
                     atomicOr(status, 4);
+                    fail = 1;
                     break;
                 }
             }
         }
         __threadfence();
+        s_fail = fail;
     }
+    ++nb;
     __syncthreads();
-    return !(*(volatile int*)status & 4);
+    return s_fail == 0;
 }
 
-// All n_macro x (forward + backward) colour sweeps of the macro PR-SGS in one
-// cooperative launch; the cells of a colour are strided over the grid, colours are
-// separated by grid barriers.  Same order and arithmetic as k_macro_sweep.
 template <typename T>
 __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cell, const int* col_off,
                                                     int C, int n_macro, unsigned int* bar) {
     const int stride = (gridDim.x * blockDim.x) / MACRO_LANES;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
     const int g = (int)(threadIdx.x % MACRO_LANES);
+    unsigned int nb = 0;
     for (int it = 0; it < n_macro; ++it) {
         for (int dir = 0; dir < 2; ++dir) {
             for (int cc = 0; cc < C; ++cc) {
@@ -1188,7 +1196,7 @@ __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cel
                 const int lo = col_off[col], hi = col_off[col + 1];
                 const int ff = (it == 0 && dir == 0);
                 for (int t = lo + gid; t < hi; t += stride) macro_point(c, t, col_cell[t], col, ff, g);
-                if (!grid_barrier(bar, c.status)) return;
+                if (!grid_barrier(bar, c.status, nb)) return;
             }
         }
     }

@@ -142,14 +142,19 @@ class Workload:
 # ----------------------------------------------------------------------------------
 # helpers
 # ----------------------------------------------------------------------------------
-def greedy_colour(n_cell: int, face_cell: np.ndarray) -> np.ndarray:
+def greedy_colour(n_cell: int, face_cell: np.ndarray, max_colours: int = 0) -> np.ndarray:
     """Deterministic greedy colouring in cell-index order: each cell takes the
-    smallest colour not used by an already coloured face neighbour."""
+    smallest colour not used by an already coloured face neighbour.  With
+    max_colours > 0, cells left with a larger colour are then moved into the first
+    max_colours colours where possible, directly or by swapping the two colours of a
+    Kempe chain around them (a mesh whose cells have at most 4 neighbours is
+    4-colourable unless it contains 5 mutually adjacent cells); cells that cannot be
+    moved keep their colour, so the result is always a proper colouring."""
     nbrs = [[] for _ in range(n_cell)]
     for a, b in face_cell:
         if b >= 0:
-            nbrs[a].append(b)
-            nbrs[b].append(a)
+            nbrs[a].append(int(b))
+            nbrs[b].append(int(a))
     colour = np.full(n_cell, -1, dtype=np.int32)
     for i in range(n_cell):
         used = {int(colour[j]) for j in nbrs[i] if colour[j] >= 0}
@@ -157,7 +162,58 @@ def greedy_colour(n_cell: int, face_cell: np.ndarray) -> np.ndarray:
         while c in used:
             c += 1
         colour[i] = c
-    return colour
+    if max_colours <= 0:
+        return colour
+    for v in np.nonzero(colour >= max_colours)[0].tolist():
+        used = {int(colour[j]) for j in nbrs[v]}
+        free = [c for c in range(max_colours) if c not in used]
+        if free:
+            colour[v] = free[0]
+            continue
+        moved = False
+        for a in range(max_colours):
+            for b in range(a + 1, max_colours):
+                # Kempe chain of colours (a, b) from v's neighbours of colour a
+                starts = [j for j in nbrs[v] if colour[j] == a]
+                seen, stack = set(starts), list(starts)
+                while stack:
+                    x = stack.pop()
+                    for y in nbrs[x]:
+                        if y not in seen and colour[y] in (a, b):
+                            seen.add(y)
+                            stack.append(y)
+                if any(colour[j] == b for j in nbrs[v] if j in seen):
+                    continue                      # the chain reaches a neighbour of colour b
+                for x in seen:
+                    colour[x] = b if colour[x] == a else a
+                colour[v] = a
+                moved = True
+                break
+            if moved:
+                break
+    # balance the classes: in cell order, move a cell from a class above the mean
+    # size into the smallest class its neighbours leave free (sweeps of the colour
+    # order are then launches of similar size)
+    C = int(colour.max()) + 1
+    size = np.bincount(colour, minlength=C).astype(np.int64)
+    mean = n_cell / C
+    for v in range(n_cell):
+        cv = int(colour[v])
+        if size[cv] <= mean:
+            continue
+        used = {int(colour[j]) for j in nbrs[v]}
+        cand = [c for c in range(C) if c not in used and c != cv and size[c] < mean]
+        if cand:
+            c = min(cand, key=lambda x: (size[x], x))
+            colour[v] = c
+            size[cv] -= 1
+            size[c] += 1
+    # renumber so that the colours in use are 0..C-1 (largest classes first)
+    vals, counts = np.unique(colour, return_counts=True)
+    order = vals[np.argsort(-counts, kind="stable")]
+    remap = np.empty(order.max() + 1, dtype=np.int32)
+    remap[order] = np.arange(len(order), dtype=np.int32)
+    return remap[colour]
 
 
 def _morton_key(p: np.ndarray, bits: int = 10) -> np.ndarray:
@@ -240,7 +296,7 @@ def _tets_to_mesh(pts, tets, keep, wall_test, name):
     mesh = Mesh(face_cell=face_cell, face_normal=nrm[fo], face_area=area[fo],
                 face_center=fc[fo], cell_center=cen, cell_volume=vol,
                 cell_colour=np.zeros(nt, dtype=np.int32), name=name)
-    mesh.cell_colour = greedy_colour(nt, face_cell)
+    mesh.cell_colour = greedy_colour(nt, face_cell, max_colours=4)
     return mesh
 
 
