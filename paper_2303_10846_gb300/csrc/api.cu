@@ -278,7 +278,7 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.macroF = cv.take<double>(6 * N); d.dW = cv.take<double>(6 * N); d.Wt = cv.take<double>(6 * N);
     d.ceq = cv.take<double>(rk::CEQ * N); d.taut = cv.take<double>(N); d.S = cv.take<double>(12 * N);
     d.cellres = cv.take<double>(12 * N); d.res12 = cv.take<double>(16);
-    d.mPc = cv.take<double>(8 * N); d.mDb = cv.take<double>(4 * N);
+    d.mPc = cv.take<double>(8 * N); d.mDb = cv.take<double>(4 * N); d.mB = cv.take<double>(12 * N);
     d.sG0 = cv.take<double>(6 * nnz); d.sC = cv.take<double>(2 * nnz);
     d.pos_off = cv.take<int>(N + 1); d.cell_pos = cv.take<int>(N);
     d.pslot_nbr = cv.take<int>(nnz); d.pslot_ncol = cv.take<int>(nnz);

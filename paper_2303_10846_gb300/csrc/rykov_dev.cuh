@@ -81,6 +81,7 @@ struct DevBase {
     // current iterate per cell, diagonal base per cell, per-slot Euler flux of the
     // neighbour's W^n and the coefficients A/(2V), A r/(2V)
     double *mPc, *mDb, *sG0, *sC;        // mDb: [N][4] = 1/D, 1/(D + 1/(Z tau)), 1/(Z tau)
+    double* mB;                          // [N][12]: F_i - sum_j (A/2V) G_ij(W_j^n), all / lower-colour j
     // the slots again, ordered by colour position (cells in col_cell order), so that a
     // macro point update finds its slot range from its position without first loading
     // the cell index: slot base per position [N+1], position of each cell [N],
@@ -1039,6 +1040,12 @@ __global__ void k_macro_prep(Dev<T> c) {
     const double iv = 1.0 / c.vol[i];
     double D = 1.0 / (cfl * c.dt[i]);
     const int ps = c.pos_off[c.cell_pos[i]];
+    // the constant part of every point update: macro flux minus the neighbours' W^n
+    // fluxes, over all interior neighbours (later sweeps) and over the lower-colour
+    // ones only (the first forward sweep, where the others are still zero)
+    double B[6], Bff[6];
+    for (int q = 0; q < 6; ++q) B[q] = Bff[q] = c.macroF[6 * (size_t)i + q];
+    const int col = c.colour[i];
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
         const int f = c.slot_face[m], j = c.slot_nbr[m];
         const size_t mp = (size_t)(ps + m - c.slot_off[i]);
@@ -1048,9 +1055,18 @@ __global__ void k_macro_prep(Dev<T> c) {
         c.sC[2 * mp + 1] = 0.5 * A * c.rf[f];
         if (j >= 0) {
             const double sg = c.slot_left[m] ? 1.0 : -1.0;
-            euler_flux(c.W + 6 * (size_t)j, sg * c.fn[f], sg * c.fn[c.F + f], sg * c.fn[2 * c.F + f],
-                       c.sG0 + 6 * mp);
+            double* G0 = c.sG0 + 6 * mp;
+            euler_flux(c.W + 6 * (size_t)j, sg * c.fn[f], sg * c.fn[c.F + f], sg * c.fn[2 * c.F + f], G0);
+            const bool lower = c.slot_ncol[m] < col;
+            for (int q = 0; q < 6; ++q) {
+                B[q] -= 0.5 * A * G0[q];
+                if (lower) Bff[q] -= 0.5 * A * G0[q];
+            }
         }
+    }
+    for (int q = 0; q < 6; ++q) {
+        c.mB[12 * (size_t)i + q] = B[q];
+        c.mB[12 * (size_t)i + 6 + q] = Bff[q];
     }
     const Prim p = prim_from_W(c.W + 6 * (size_t)i, c.R);
     const double izt = 1.0 / (c.Z * relax_time(c, p.rho, p.Ttr));
@@ -1078,7 +1094,14 @@ __global__ void k_macro_prep(Dev<T> c) {
 template <typename T>
 __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int colour, int first_forward,
                                             int g) {
+    // o = F - sum_j (A/2V) G_ij(W_j^n) + sum_j (A/2V) G_ij(W_j + dW~_j) - (A r/2V) dW~_j:
+    // lane 0 starts from the per-cell constant part, every lane adds its faces
     double o[6] = {0, 0, 0, 0, 0, 0};
+    if (g == 0) {
+        const double* B = c.mB + 12 * (size_t)i + (first_forward ? 6 : 0);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) o[q] = B[q];
+    }
     for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += MACRO_LANES) {
         const int j = c.pslot_nbr[m];
         if (j < 0 || (first_forward && c.pslot_ncol[m] > colour)) continue;
@@ -1094,10 +1117,9 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int c
         const double rU = P[0] * Un;
         const double G1[6] = {rU, rU * P[1] + P[5] * nx, rU * P[2] + P[5] * ny, rU * P[3] + P[5] * nz,
                               P[4] * Un, P[6] * Un};
-        const double* G0 = c.sG0 + 6 * (size_t)m;
         const double c1 = c.sC[2 * (size_t)m], c2 = c.sC[2 * (size_t)m + 1];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) o[q] += c1 * (G1[q] - G0[q]) - c2 * dWj[q];
+        for (int q = 0; q < 6; ++q) o[q] += c1 * G1[q] - c2 * dWj[q];
     }
     if (MACRO_LANES > 1) {
         const unsigned mask = MACRO_LANES == 32 ? 0xffffffffu
@@ -1108,22 +1130,16 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int c
             for (int q = 0; q < 6; ++q) o[q] += __shfl_xor_sync(mask, o[q], off);
     }
     const double* W = c.W + 6 * (size_t)i;
-    double* dW = c.dW + 6 * (size_t)i;
-    double dWi[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) dWi[q] = __ldcg(dW + q);
-    // rho R T of the current iterate: (2/5)(rho E - |rho U|^2 / (2 rho))
-    const double rc = W[0] + dWi[0];
-    const double mx = W[1] + dWi[1], my = W[2] + dWi[2], mz = W[3] + dWi[3];
-    const double rRT = 0.4 * (W[4] + dWi[4] - 0.5 * (mx * mx + my * my + mz * mz) / rc);
-    const double* F = c.macroF + 6 * (size_t)i;
+    // rho R T of the current iterate: its cached pressure p = (2/5)(rho E - 1/2 rho |U|^2)
+    const double rRT = __ldcg(c.mPc + 8 * (size_t)i + 5);
     const double iD = c.mDb[4 * (size_t)i], iDr = c.mDb[4 * (size_t)i + 1], izt = c.mDb[4 * (size_t)i + 2];
     double cand[6];
-    for (int q = 0; q < 5; ++q) cand[q] = (-F[q] - o[q]) * iD;
-    cand[5] = ((rRT - W[5]) * izt - F[5] - o[5]) * iDr;
+    for (int q = 0; q < 5; ++q) cand[q] = -o[q] * iD;
+    cand[5] = ((rRT - W[5]) * izt - o[5]) * iDr;
     double Wn[6], Pn[8];
     for (int q = 0; q < 6; ++q) Wn[q] = W[q] + cand[q];
     if (!flux_prim(Wn, Pn) || g != 0) return;
+    double* dW = c.dW + 6 * (size_t)i;
     for (int q = 0; q < 6; ++q) __stcg(dW + q, cand[q]);
     for (int q = 0; q < 8; ++q) __stcg(c.mPc + 8 * (size_t)i + q, Pn[q]);
 }
