@@ -59,6 +59,8 @@ extern "C" int rk_destroy(rk_ctx* ctx) {
     if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_bnd) cudaEventDestroy(ctx->ev_bnd);
+    if (ctx->ev_int) cudaEventDestroy(ctx->ev_int);
     delete ctx;
     return RK_OK;
 }
@@ -540,16 +542,25 @@ static int build_graph(rk_ctx* ctx, rk::Dev<T>& d) {
     if (!ctx->cap2) CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
     if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    if (!ctx->ev_bnd) CK(cudaEventCreateWithFlags(&ctx->ev_bnd, cudaEventDisableTiming));
+    if (!ctx->ev_int) CK(cudaEventCreateWithFlags(&ctx->ev_int, cudaEventDisableTiming));
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     // reconstruction and faces; then two branches: the micro flux gather on a second
     // stream while the macro fluxes and the macro PR-SGS (latency-bound, few SMs busy)
     // run on the first; joined before the micro sweeps
+    // the boundary faces run beside the interior faces (both only read phi(x_f - u s)
+    // of their own faces)
     cudaError_t e = launch_step(ctx, d, RK_STEP_RECON, ctx->cap);
-    if (e == cudaSuccess) e = launch_step(ctx, d, RK_STEP_FACES, ctx->cap);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, ctx->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap2, ctx->ev_fork, 0);
+    if (e == cudaSuccess) e = rk::Launch<T>::faces_boundary(d, ctx->cap2, ctx->prof);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_bnd, ctx->cap2);
+    if (e == cudaSuccess) e = rk::Launch<T>::faces_interior(d, ctx->cap, ctx->prof);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_int, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap2, ctx->ev_int, 0);
     if (e == cudaSuccess) e = rk::Launch<T>::micro_flux(d, ctx->cap2, ctx->prof);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->cap2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_bnd, 0);
     if (e == cudaSuccess) e = rk::Launch<T>::fluxes(d, ctx->cap, ctx->prof);
     if (e == cudaSuccess) e = launch_step(ctx, d, RK_STEP_MACRO, ctx->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);

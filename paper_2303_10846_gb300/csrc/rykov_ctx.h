@@ -78,7 +78,7 @@ struct rk_ctx {
     bool use_graph = true;
     bool use_coop = false;            // cooperative launch of the macro PR-SGS (RYKOV_COOP=1)
     cudaStream_t cap = nullptr, cap2 = nullptr;   // capture streams (main, side branch)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bnd = nullptr, ev_int = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long graph_kernels = 0;
     double last_res[6] = {0, 0, 0, 0, 0, 0};

@@ -32,7 +32,7 @@ constexpr int MAXF = 8;        // faces per cell
 #define MICRO_FIRST_NV 4
 #endif
 #ifndef MICRO_MID_MINB
-#define MICRO_MID_MINB 4
+#define MICRO_MID_MINB 5
 #endif
 #ifndef MICRO_LAST_MINB
 #define MICRO_LAST_MINB 4
@@ -722,6 +722,7 @@ template <typename T, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
     using R = Red<T>;
     using V = typename R::V;
+    constexpr int NV = VW<T>::N;
     const int lane = threadIdx.x & 31;
     const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
     if (fi >= c.Fi) return;                      // whole warp: no block barriers below
@@ -746,22 +747,35 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
         // compensated: the conserved moments (0-4); plain per-lane FP32 sums (<= K/32
         // terms each, then float-float across lanes): the second and third moments,
         // which only enter the heat-flux correction
+        // NV consecutive velocities per lane (8-byte loads in mixed mode); their terms
+        // are summed plainly, then added with compensation
         Acc<T> m[5];
         T p2[12];
 #pragma unroll
         for (int j = 0; j < 12; ++j) p2[j] = T(0);
-        for (int k = lane; k < c.K; k += 32) {
-            const T cx = c.uT[k] - Ur[0], cy = c.uT[c.Kp + k] - Ur[1], cz = c.uT[2 * c.Kp + k] - Ur[2];
-            const T w = c.wT[k];
-            const T wg = w * g0[k], wh = w * h0[k];
-            m[0].add(wg);
-            m[1].add(wg * cx); m[2].add(wg * cy); m[3].add(wg * cz);
-            m[4].add(wh);
-            p2[0] += wg * cx * cx; p2[1] += wg * cy * cy; p2[2] += wg * cz * cz;
-            p2[3] += wg * cx * cy; p2[4] += wg * cx * cz; p2[5] += wg * cy * cz;
-            const T wgc2 = wg * (cx * cx + cy * cy + cz * cz);
-            p2[6] += wgc2 * cx; p2[7] += wgc2 * cy; p2[8] += wgc2 * cz;
-            p2[9] += wh * cx; p2[10] += wh * cy; p2[11] += wh * cz;
+        for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+            T ux[NV], uy[NV], uz[NV], wv[NV], gv[NV], hv[NV], t[5];
+            vload(c.uT + k0, ux);
+            vload(c.uT + c.Kp + k0, uy);
+            vload(c.uT + 2 * c.Kp + k0, uz);
+            vload(c.wT + k0, wv);
+            vload(g0 + k0, gv);
+            vload(h0 + k0, hv);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                const T cx = ux[e] - Ur[0], cy = uy[e] - Ur[1], cz = uz[e] - Ur[2];
+                const T wg = wv[e] * gv[e], wh = wv[e] * hv[e];
+                const T tv[5] = {wg, wg * cx, wg * cy, wg * cz, wh};
+#pragma unroll
+                for (int j = 0; j < 5; ++j) t[j] = e == 0 ? tv[j] : t[j] + tv[j];
+                p2[0] += wg * cx * cx; p2[1] += wg * cy * cy; p2[2] += wg * cz * cz;
+                p2[3] += wg * cx * cy; p2[4] += wg * cx * cz; p2[5] += wg * cy * cz;
+                const T wgc2 = wg * (cx * cx + cy * cy + cz * cz);
+                p2[6] += wgc2 * cx; p2[7] += wgc2 * cy; p2[8] += wgc2 * cz;
+                p2[9] += wh * cx; p2[10] += wh * cy; p2[11] += wh * cz;
+            }
+#pragma unroll
+            for (int j = 0; j < 5; ++j) m[j].add(t[j]);
         }
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] = R::from(m[j]);
@@ -829,19 +843,36 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
     V r6[6];
     {
         Acc<T> m[6];
-        for (int k = lane; k < c.K; k += 32) {
-            const T ux = c.uT[k], uy = c.uT[c.Kp + k], uz = c.uT[2 * c.Kp + k], w = c.wT[k];
-            T G, H;
-            eval_eq(e + 2, ux, uy, uz, G, H);
-            const T gf = a * g0[k] + b * G;
-            const T hf = a * h0[k] + b * H;
-            g0[k] = gf;
-            h0[k] = hf;
-            const T wu = w * (ux * nx + uy * ny + uz * nz);
-            const T wg = wu * gf;
-            m[0].add(wg); m[1].add(wg * ux); m[2].add(wg * uy); m[3].add(wg * uz);
-            m[4].add(wu * (T(0.5) * (ux * ux + uy * uy + uz * uz) * gf + hf));
-            m[5].add(wu * hf);
+        for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+            T ux[NV], uy[NV], uz[NV], wv[NV], gv[NV], hv[NV], t[6];
+            vload(c.uT + k0, ux);
+            vload(c.uT + c.Kp + k0, uy);
+            vload(c.uT + 2 * c.Kp + k0, uz);
+            vload(c.wT + k0, wv);
+            vload(g0 + k0, gv);
+            vload(h0 + k0, hv);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                T G, H;
+                eval_eq(e + 2, ux[q], uy[q], uz[q], G, H);
+                // the K padding keeps zero face values
+                const bool pad = k0 + q >= c.K;
+                const T gf = pad ? T(0) : a * gv[q] + b * G;
+                const T hf = pad ? T(0) : a * hv[q] + b * H;
+                gv[q] = gf;
+                hv[q] = hf;
+                const T wu = wv[q] * (ux[q] * nx + uy[q] * ny + uz[q] * nz);
+                const T wg = wu * gf;
+                const T tv[6] = {wg, wg * ux[q], wg * uy[q], wg * uz[q],
+                                 wu * (T(0.5) * (ux[q] * ux[q] + uy[q] * uy[q] + uz[q] * uz[q]) * gf + hf),
+                                 wu * hf};
+#pragma unroll
+                for (int j = 0; j < 6; ++j) t[j] = q == 0 ? tv[j] : t[j] + tv[j];
+            }
+            vstore(g0 + k0, gv);
+            vstore(h0 + k0, hv);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) m[j].add(t[j]);
         }
 #pragma unroll
         for (int j = 0; j < 6; ++j) r6[j] = R::from(m[j]);
@@ -1091,6 +1122,9 @@ __global__ void k_macro_prep(Dev<T> c) {
 #ifndef MACRO_LANES
 #define MACRO_LANES 2
 #endif
+#ifndef MACRO_FINAL_ONE
+#define MACRO_FINAL_ONE 0
+#endif
 template <typename T>
 __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int colour, int first_forward,
                                             int g) {
@@ -1129,6 +1163,9 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int c
 #pragma unroll
             for (int q = 0; q < 6; ++q) o[q] += __shfl_xor_sync(mask, o[q], off);
     }
+#if MACRO_FINAL_ONE
+    if (g != 0) return;                  // the update itself on one lane of the group
+#endif
     const double* W = c.W + 6 * (size_t)i;
     // rho R T of the current iterate: its cached pressure p = (2/5)(rho E - 1/2 rho |U|^2)
     const double rRT = __ldcg(c.mPc + 8 * (size_t)i + 5);
@@ -1427,6 +1464,8 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
         if (last) {
             T g1[NV], h1[NV], wv[NV];
             vload(c.wT + k0, wv);
+            // the lane's NV terms are summed plainly, then added with compensation
+            T t[12];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 g1[v] = pg[v] + xg[v];
@@ -1435,13 +1474,15 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
                 const T cx = ux[v] - e[0], cy = uy[v] - e[1], cz = uz[v] - e[2];
                 const T c2 = cx * cx + cy * cy + cz * cz;
                 const T wg = wv[v] * Dg, wh = wv[v] * Dh;
-                a[0].add(wg); a[1].add(wg * ux[v]); a[2].add(wg * uy[v]); a[3].add(wg * uz[v]);
-                a[4].add(T(0.5) * (ux[v] * ux[v] + uy[v] * uy[v] + uz[v] * uz[v]) * wg + wh);
-                a[5].add(wh);
                 const T wgc = wg * c2;
-                a[6].add(wgc * cx); a[7].add(wgc * cy); a[8].add(wgc * cz);
-                a[9].add(wh * cx); a[10].add(wh * cy); a[11].add(wh * cz);
+                const T tv[12] = {wg, wg * ux[v], wg * uy[v], wg * uz[v],
+                                  T(0.5) * (ux[v] * ux[v] + uy[v] * uy[v] + uz[v] * uz[v]) * wg + wh, wh,
+                                  wgc * cx, wgc * cy, wgc * cz, wh * cx, wh * cy, wh * cz};
+#pragma unroll
+                for (int j = 0; j < 12; ++j) t[j] = v == 0 ? tv[j] : t[j] + tv[j];
             }
+#pragma unroll
+            for (int j = 0; j < 12; ++j) a[j].add(t[j]);
             vstore(c.phi + oi + k0, g1);
             vstore(c.phi + NK + oi + k0, h1);
         }

@@ -45,7 +45,9 @@ struct Launch {
     static cudaError_t set_state(const Dev<T>& d, cudaStream_t s, const double* prim,
                                  const double* q);
     static cudaError_t recon(const Dev<T>& d, cudaStream_t s, Prof& pf);
-    static cudaError_t faces(const Dev<T>& d, cudaStream_t s, Prof& pf);
+    static cudaError_t faces(const Dev<T>& d, cudaStream_t s, Prof& pf);   // interior + boundary
+    static cudaError_t faces_interior(const Dev<T>& d, cudaStream_t s, Prof& pf);
+    static cudaError_t faces_boundary(const Dev<T>& d, cudaStream_t s, Prof& pf);
     static cudaError_t fluxes(const Dev<T>& d, cudaStream_t s, Prof& pf);
     // micro flux F into res: independent of the macro solve (a parallel graph branch)
     static cudaError_t micro_flux(const Dev<T>& d, cudaStream_t s, Prof& pf);

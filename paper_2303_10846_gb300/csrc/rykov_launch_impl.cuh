@@ -39,13 +39,18 @@ cudaError_t Launch<T>::recon(const Dev<T>& d, cudaStream_t s, Prof& pf) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::faces(const Dev<T>& d, cudaStream_t s, Prof& pf) {
+cudaError_t Launch<T>::faces_interior(const Dev<T>& d, cudaStream_t s, Prof& pf) {
     if (d.Fi) {
         pf.begin(1, s);
         k_face_interior<T, FACE_WPB><<<cdiv(d.Fi, FACE_WPB), FACE_WPB * 32, 0, s>>>(d);
         pf.end(s);
         pf.launches += 1;
     }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::faces_boundary(const Dev<T>& d, cudaStream_t s, Prof& pf) {
     if (d.Fb) {
         pf.begin(2, s);
         k_face_boundary<T, FACE_BS><<<d.Fb, FACE_BS, 0, s>>>(d);
@@ -53,6 +58,12 @@ cudaError_t Launch<T>::faces(const Dev<T>& d, cudaStream_t s, Prof& pf) {
         pf.launches += 1;
     }
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::faces(const Dev<T>& d, cudaStream_t s, Prof& pf) {
+    cudaError_t e = faces_interior(d, s, pf);
+    return e != cudaSuccess ? e : faces_boundary(d, s, pf);
 }
 
 template <typename T>
