@@ -35,7 +35,8 @@ class OrcParams(C.Structure):
                 ("lim_k", C.c_double),
                 ("n_micro_sgs", C.c_int32), ("n_macro_sgs", C.c_int32),
                 ("limiter", C.c_int32), ("first_order_iters", C.c_int32),
-                ("limiter_freeze", C.c_int32)]
+                ("limiter_freeze", C.c_int32), ("viscosity_law", C.c_int32),
+                ("sutherland_c", C.c_double)]
 
 
 class OrcState(C.Structure):

@@ -112,7 +112,10 @@ class Steady:
 
     # ------------------------------------------------------------ gas relations ---
     def viscosity(self, Ttr):
-        return self.P.mu_ref * (Ttr / self.P.T_ref) ** self.P.omega_vis       # Eq. T_solve_mu
+        P = self.P
+        if P.viscosity_law == 1:                                              # Eq. T_solve_mu_Sut
+            return P.mu_ref * (Ttr / P.T_ref) ** 1.5 * (P.T_ref + P.sutherland_c) / (Ttr + P.sutherland_c)
+        return P.mu_ref * (Ttr / P.T_ref) ** P.omega_vis                       # Eq. T_solve_mu
 
     def prim(self, W):
         """rho, U, T, T_tr, T_rot from W (K_tr = 3, K_rot = 2), Eqs. f_solve_rho -

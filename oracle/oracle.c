@@ -59,8 +59,13 @@ static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1]
 #define LSTORE(fd, i, k) c->lstore[((size_t)(fd) * (size_t)c->N + (size_t)(i)) * (size_t)c->K + (size_t)(k)]
 #define GRAD(fd, d, i, k) c->grad[(((size_t)(fd) * 3 + (size_t)(d)) * (size_t)c->N + (size_t)(i)) * (size_t)c->K + (size_t)(k)]
 
-/* VHS viscosity, Eq. T_solve_mu. */
-static double viscosity(const orc_params* P, double Ttr) { return P->mu_ref * pow(Ttr / P->T_ref, P->omega_vis); }
+/* Viscosity of the translational temperature: the power law of Eq. T_solve_mu, or
+ * Sutherland's formula, Eq. T_solve_mu_Sut (chosen by viscosity_law). */
+static double viscosity(const orc_params* P, double Ttr) {
+    if (P->viscosity_law == 1)
+        return P->mu_ref * pow(Ttr / P->T_ref, 1.5) * (P->T_ref + P->sutherland_c) / (Ttr + P->sutherland_c);
+    return P->mu_ref * pow(Ttr / P->T_ref, P->omega_vis);
+}
 
 /* Relaxation time tau = mu(T_tr) / p_tr (Sec. 2.1, text after Eq. frot). */
 static double relax_time(const orc_params* P, double rho, double Ttr) {

@@ -42,6 +42,9 @@ typedef struct {
     int32_t first_order_iters; /* iterations run first order after set_state      */
     int32_t limiter_freeze;    /* > 0: from this iteration on the limiter values of
                                   iteration limiter_freeze - 1 are reused (0: never) */
+    int32_t viscosity_law;     /* 0: power law (omega_vis), Eq. T_solve_mu;
+                                  1: Sutherland's law (sutherland_c), Eq. T_solve_mu_Sut */
+    double sutherland_c;       /* Sutherland constant C_s in units of temperature  */
 } orc_params;
 
 enum { ORC_WALL = 0, ORC_FARFIELD = 1 };

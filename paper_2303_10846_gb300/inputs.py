@@ -110,6 +110,8 @@ class Params:
     limiter: int = 1          # 0 unlimited, 1 Venkatakrishnan, 2 first order
     first_order_iters: int = 0
     limiter_freeze: int = 0   # > 0: limiter values of iteration limiter_freeze - 1 reused
+    viscosity_law: int = 0    # 0 power law (omega_vis), 1 Sutherland (sutherland_c)
+    sutherland_c: float = 111.0 / 273.0   # C_s of nitrogen (111 K) over a 273 K unit
 
     def as_dict(self):
         return asdict(self)

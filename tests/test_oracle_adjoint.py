@@ -37,7 +37,14 @@ def _state(o, st):
             torch.as_tensor(o.get(O.BUF_Q)))
 
 
-@pytest.mark.parametrize("make", [tiny_cavity, lambda: tiny_tet(n_gh=4)], ids=["cavity", "tet"])
+def _tet_sutherland():
+    wl = tiny_tet(n_gh=4)
+    wl.params = dataclasses.replace(wl.params, viscosity_law=1, sutherland_c=0.4)
+    return wl
+
+
+@pytest.mark.parametrize("make", [tiny_cavity, lambda: tiny_tet(n_gh=4), _tet_sutherland],
+                         ids=["cavity", "tet", "tet-sutherland"])
 def test_flux_and_gradient_match_c_oracle(make):
     wl = _second_order(make())
     o = O.Oracle(wl)
@@ -106,12 +113,14 @@ def test_closed_cavity_conserves_energy_and_momentum():
     assert abs(float(dJdp[0])) < 1e-10 * scale
 
 
-@pytest.mark.parametrize("lim,h", [(0, 1e-6), (1, 1e-7), (2, 1e-6)])
-def test_vjp_is_the_transpose_of_the_finite_difference_jvp(lim, h):
+@pytest.mark.parametrize("lim,h,law", [(0, 1e-6, 0), (1, 1e-7, 0), (2, 1e-6, 0), (0, 1e-6, 1)])
+def test_vjp_is_the_transpose_of_the_finite_difference_jvp(lim, h, law):
     """<v, J u> by central differences equals <J^T v, u> (the limiter's min/max kinks
-    are crossed by the wider steps, hence the smaller step with the limiter on)."""
+    are crossed by the wider steps, hence the smaller step with the limiter on); law 1
+    takes Sutherland's viscosity, whose temperature slope enters through tau."""
     wl = tiny_tet(n_gh=4)
-    wl.params = dataclasses.replace(wl.params, first_order_iters=0, limiter=lim)
+    wl.params = dataclasses.replace(wl.params, first_order_iters=0, limiter=lim,
+                                    viscosity_law=law, sutherland_c=0.4)
     o = O.Oracle(wl)
     o.iterate(3)
     st = Steady(wl)
