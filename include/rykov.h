@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define RK_VERSION 101
+#define RK_VERSION 102
 
 enum {
     RK_OK = 0,
@@ -77,6 +77,10 @@ typedef struct rk_params {
                                   limiter_freeze - 1 (no counterpart in the paper: the
                                   limiter's switching otherwise stalls the residual);
                                   0: never                                        */
+    int32_t viscosity_law;     /* 0: power law mu_ref (T_tr/T_ref)^omega_vis,
+                                  Eq. T_solve_mu; 1: Sutherland's law with constant
+                                  sutherland_c, Eq. T_solve_mu_Sut                 */
+    double sutherland_c;       /* C_s >= 0 in the units of T (111 K for nitrogen) */
 } rk_params;
 
 typedef struct rk_ctx rk_ctx;
@@ -212,10 +216,11 @@ int rk_profile_get(rk_ctx* ctx, double* ms, int64_t* counts);
  * It allocates nothing: its scratch (per-block partial sums, 12 doubles per 256
  * cells) is one fixed array of RK_NOALLOC_MAX_CELLS / 256 * 12 doubles (384 KiB)
  * in the library's device memory, which every GPU that loads the library holds
- * until the process exits.  All calls share that array: calls whose work overlaps
- * on the GPU (different streams, or devices are fine) race on it and give wrong
- * results.  Each call overwrites every part of the array it reads, so nothing
- * carries over from one call to the next.  The first call on a device (with that
+ * until the process exits.  All calls on one device share that array: calls whose
+ * work overlaps on that GPU (for instance on two streams) race on it and give wrong
+ * results; calls on different devices do not, each device having its own copy.
+ * Each call overwrites every part of the array it reads, so nothing carries over
+ * from one call to the next.  The first call on a device (with that
  * device current) looks the array's device address up once; make that first call
  * before any stream capture.  Returns RK_OK, RK_EINVAL (null pointer, bad size) or
  * RK_ECUDA; rk_noalloc_last_error() gives the message of the last failed call on

@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a,
     const double atr = (1.0 / 3.0) * (1.0 - (1.0 - c.omega0) / Z);
     const double arot = (1.0 - c.delta) * (1.0 - (1.0 - c.omega1) / Z);
     for (int d = 0; d < 3; ++d) { qb[d] += vq[d] * (atr - 1.0); qb[3 + d] += vq[3 + d] * (arot - 1.0); }
-    // tau = mu(T_tr) / (rho R T_tr), mu ~ T_tr^omega
-    Ttrb += taub * tau * (c.omega_vis - 1.0) / p.Ttr;
+    // tau = mu(T_tr) / (rho R T_tr); d ln mu / d ln T_tr from the viscosity law
+    Ttrb += taub * tau * (viscosity_slope(c, p.Ttr) - 1.0) / p.Ttr;
     rb -= taub * tau / p.rho;
     // primitives from W
     const double k15 = 1.0 / (1.5 * p.rho * R), k25 = 1.0 / (2.5 * p.rho * R), kr = 1.0 / (p.rho * R);
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
     double Er0b = Erotb * Z * tau / den;
     rb += Erotb * s * Rg * T / den;
     Tb += Erotb * s * rho * Rg / den;
-    const double Ttr0b = taub * tau * (c.omega_vis - 1.0) / Ttr0;
+    const double Ttr0b = taub * tau * (viscosity_slope(c, Ttr0) - 1.0) / Ttr0;
     rb -= taub * tau / rho;
     Eb += Ttr0b * k15; keb -= Ttr0b * k15; Er0b -= Ttr0b * k15;
     rb -= Ttr0b * Ttr0 / rho;

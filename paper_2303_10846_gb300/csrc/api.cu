@@ -44,6 +44,7 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     d.omega0 = 0.2354; d.omega1 = 0.3049; d.delta = 1.0 / 1.55; d.cfl_s = 0.8;
     d.cfl_imp = 1e3; d.cfl_imp0 = 0.0; d.cfl_ramp = 1.0; d.lim_k = 0.1;
     d.n_micro_sgs = 2; d.n_macro_sgs = 40; d.limiter = 1; d.first_order_iters = 0;
+    d.limiter_freeze = 0; d.viscosity_law = 0; d.sutherland_c = 111.0 / 273.0;
     ctx->p = d;
     *out = ctx;
     return RK_OK;
@@ -72,7 +73,8 @@ extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
     if (!(p->R > 0) || !(p->Z_rot >= 1.0) || !(p->mu_ref > 0) || !(p->T_ref > 0) ||
         !(p->cfl_s > 0) || !(p->cfl_imp > 0) || p->n_micro_sgs < 1 || p->n_macro_sgs < 0 ||
         p->limiter < 0 || p->limiter > 2 || !(p->lim_k >= 0) || p->limiter_freeze < 0 ||
-        (p->limiter_freeze > 0 && p->limiter_freeze <= p->first_order_iters))
+        (p->limiter_freeze > 0 && p->limiter_freeze <= p->first_order_iters) ||
+        (p->viscosity_law != 0 && p->viscosity_law != 1) || !(p->sutherland_c >= 0))
         return fail(ctx, RK_EINVAL, "rk_set_params: parameter out of range");
     bool geo_change = ctx->p.cfl_s != p->cfl_s || ctx->p.lim_k != p->lim_k;
     ctx->p = *p;
@@ -92,6 +94,7 @@ extern "C" int rk_set_params(rk_ctx* ctx, const rk_params* p) {
         d.cfl_imp = p->cfl_imp; d.cfl_imp0 = p->cfl_imp0; d.cfl_ramp = p->cfl_ramp;
         d.first_order_iters = p->first_order_iters; d.limiter = p->limiter;
         d.limiter_freeze = p->limiter_freeze;
+        d.viscosity_law = p->viscosity_law; d.sutherland_c = p->sutherland_c;
         using TT = std::remove_reference_t<decltype(d.tp[0])>;
         const double v[8] = {p->R, p->Z_rot, p->mu_ref, p->T_ref, p->omega_vis, p->omega0, p->omega1, p->delta};
         for (int j = 0; j < 8; ++j) d.tp[j] = (TT)v[j];

@@ -50,6 +50,8 @@ struct DevBase {
     // implicit-step schedule, evaluated on the device each iteration (k_iter_begin)
     double cfl_imp, cfl_imp0, cfl_ramp;
     int first_order_iters, limiter, limiter_freeze;
+    int viscosity_law;                 // 0 power law, 1 Sutherland
+    double sutherland_c;               // Sutherland constant C_s
     // [0] cfl, [1] reconstruction mode (0 unlimited, 1 limited, 2 first order,
     // 3 limited with the stored limiter values, 4 limited and store them), [2] counter
     double* iterp;
@@ -322,7 +324,15 @@ __device__ __forceinline__ void vstore(double* p, const double (&x)[1]) { *p = x
 // ------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ double viscosity(const Dev<T>& c, double Ttr) {
+    if (c.viscosity_law == 1)                                         // Eq. T_solve_mu_Sut
+        return c.mu_ref * pow(Ttr / c.T_ref, 1.5) * (c.T_ref + c.sutherland_c) / (Ttr + c.sutherland_c);
     return c.mu_ref * pow(Ttr / c.T_ref, c.omega_vis);                 // Eq. T_solve_mu
+}
+// d ln mu / d ln T_tr of the viscosity law (for the adjoint)
+template <typename T>
+__device__ __forceinline__ double viscosity_slope(const Dev<T>& c, double Ttr) {
+    if (c.viscosity_law == 1) return 1.5 - Ttr / (Ttr + c.sutherland_c);
+    return c.omega_vis;
 }
 template <typename T>
 __device__ __forceinline__ double relax_time(const Dev<T>& c, double rho, double Ttr) {
@@ -361,6 +371,16 @@ __device__ __forceinline__ S par(const Dev<T>& c, int j) {
         const double v[8] = {c.R, c.Z, c.mu_ref, c.T_ref, c.omega_vis, c.omega0, c.omega1, c.delta};
         return (S)v[j];
     }
+}
+
+// the same law in the per-velocity arithmetic type S
+template <typename S, typename T>
+__device__ __forceinline__ S viscosity_T(const Dev<T>& c, S Ttr) {
+    if (c.viscosity_law == 1) {
+        const S Cs = (S)c.sutherland_c, Tr = par<S>(c, 3), x = Ttr / Tr;
+        return par<S>(c, 2) * x * sqrt(x) * (Tr + Cs) / (Ttr + Cs);
+    }
+    return par<S>(c, 2) * pow(Ttr / par<S>(c, 3), par<S>(c, 4));
 }
 
 template <typename T, typename S>
@@ -808,7 +828,7 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
         // tau from the translational temperature of the free-transport moments
         // (reading of the circular definition of the interface tau)
         const T Ttr0 = etr / (T(1.5) * rho * Rg);
-        const T tau = par<T>(c, 2) * pow(Ttr0 / par<T>(c, 3), par<T>(c, 4)) / (rho * Rg * Ttr0);
+        const T tau = viscosity_T<T>(c, Ttr0) / (rho * Rg * Ttr0);
         const T Erot = (Z * tau * Er0 + s * rho * Rg * Tq) / (Z * tau + s);
         const T Trot = Erot / (rho * Rg);
         const T Ttr = (etr + Er0 - Erot) / (T(1.5) * rho * Rg);

@@ -46,7 +46,8 @@ class RkParams(C.Structure):
                 ("cfl_imp", C.c_double), ("cfl_imp0", C.c_double), ("cfl_ramp", C.c_double),
                 ("lim_k", C.c_double), ("n_micro_sgs", C.c_int32), ("n_macro_sgs", C.c_int32),
                 ("limiter", C.c_int32), ("first_order_iters", C.c_int32),
-                ("limiter_freeze", C.c_int32)]
+                ("limiter_freeze", C.c_int32), ("viscosity_law", C.c_int32),
+                ("sutherland_c", C.c_double)]
 
 
 _lib = None

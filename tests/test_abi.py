@@ -23,12 +23,12 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(lib, n), f"{n} declared but not exported"
     assert sorted(rykov.EXPORTS) == sorted(names)
-    assert lib.rk_version() == 101
+    assert lib.rk_version() == 102
 
 
 def test_params_struct_layout_matches_header():
-    # 13 doubles + 5 int32, padded to a multiple of 8 bytes
-    assert ctypes.sizeof(rykov.RkParams) == 13 * 8 + 5 * 4 + 4
+    # 13 doubles + 6 int32 + 1 double
+    assert ctypes.sizeof(rykov.RkParams) == 13 * 8 + 6 * 4 + 8
     src = open(os.path.join(ROOT, "include", "rykov.h")).read()
     body = src[src.index("typedef struct rk_params"):src.index("} rk_params;")]
     fields = re.findall(r"(double|int32_t)\s+([^;]+);", body)

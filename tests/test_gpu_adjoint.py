@@ -39,7 +39,13 @@ def tet():
     return wl
 
 
-WORKLOADS = {"lid_farfield": lid_farfield, "tet": tet}
+def tet_sutherland():
+    wl = tet()
+    wl.params = dataclasses.replace(wl.params, viscosity_law=1, sutherland_c=0.4)
+    return wl
+
+
+WORKLOADS = {"lid_farfield": lid_farfield, "tet": tet, "tet_sutherland": tet_sutherland}
 
 
 def _solver_prec(wl, prec, m):

@@ -32,7 +32,15 @@ WORKLOADS = {
     "cavity4": lambda: TW.tiny_cavity(4, 6),
     "tet": lambda: TW.tiny_tet(lim=1, first_order_iters=1, cfl_imp=20.0),
     "tet_k_ragged": lambda: TW.tiny_tet(n_gh=7, lim=1, cfl_imp=20.0),      # K = 343: ragged tail
+    "tet_sutherland": lambda: _sutherland(TW.tiny_tet(lim=1, first_order_iters=1, cfl_imp=20.0)),
 }
+
+
+def _sutherland(wl):
+    """Sutherland's viscosity law (Eq. T_solve_mu_Sut) in place of the power law."""
+    import dataclasses
+    wl.params = dataclasses.replace(wl.params, viscosity_law=1, sutherland_c=0.4)
+    return wl
 
 
 @pytest.mark.parametrize("name", list(WORKLOADS))
