@@ -247,24 +247,31 @@ def run_gpu(args, rank, world, local_rank):
                 "reached": bool(rc3 == 0 and float(np.max(res3)) < 1e-6),
                 "final_residual": float(np.max(res3))}
 
-    # end to end through the public API with host buffers: upload the initial
-    # state from pinned host memory, iterate with the residual read back to the
-    # host every iteration, read W and q back
-    prim = torch.from_numpy(np.ascontiguousarray(wl.prim0)).pin_memory()
+    # end to end through the public API with host buffers: a restart from a host
+    # checkpoint (W, q and the distributions in pinned host memory, uploaded by
+    # rk_set_state), the same second-order iterations as the timed region with the
+    # residual read back to the host every iteration, then W and q read back
+    from paper_2303_10846_gb300.rykov import _ptr
+    import dataclasses
+    s.set_params(dataclasses.replace(wl.params, first_order_iters=0))
+    s.iterate(1)                                   # capture the graph for these params
     Wh = torch.empty((N, 6), dtype=torch.float64).pin_memory()
     qh = torch.empty((N, 6), dtype=torch.float64).pin_memory()
+    s._check(s.L.rk_moments(s.h, _ptr(Wh), _ptr(qh), None, 0))
+    dist = s.get_distribution().cpu().pin_memory()
     barrier()
     t1 = time.perf_counter()
-    s.set_state_prim(prim.numpy())
+    s._check(s.L.rk_set_state(s.h, _ptr(Wh), _ptr(qh), _ptr(dist), 0))
     rc2, done2, _ = s.iterate(args.steps, tol=1e-300)
-    from paper_2303_10846_gb300.rykov import _ptr
     s._check(s.L.rk_moments(s.h, _ptr(Wh), _ptr(qh), None, 0))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t1
     e2e_s = max_over_ranks(e2e_s, world, dev)
+    up = (Wh.numel() + qh.numel()) * 8 + dist.numel() * dist.element_size()
     e2e = {"value": job_value(N * K * done2, world, e2e_s * 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(prim.numel() * 8 / done2),
+           "h2d_bytes_per_step": int(up / done2),
            "d2h_bytes_per_step": int(6 * 8 + (Wh.numel() + qh.numel()) * 8 / done2)}
+    s.set_params(wl.params)
 
     # adjoint of the steady residual (FP64 arithmetic at the context's state): one
     # vector-Jacobian product, and a fixed number of GMRES iterations of the adjoint solve
