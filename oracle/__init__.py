@@ -90,6 +90,7 @@ def lib():
         L.orc_n_wall_faces.restype = i64
         L.orc_n_wall_faces.argtypes = [vp]
         L.orc_surface.argtypes = [vp, dp, vp, dp, vp, vp, vp]
+        L.orc_aero.argtypes = [vp, dp, vp, vp, dp, dp, vp, vp]
         L.orc_equilibrium.argtypes = [P(OrcParams), P(OrcState), i64, vp, vp, vp]
         L.orc_equilibrium_parts.argtypes = [P(OrcParams), P(OrcState), i64, vp, vp, vp, vp, vp]
         L.orc_interface.argtypes = [P(OrcParams), i64, vp, vp, vp, vp, dp, vp, vp, vp]
@@ -277,3 +278,18 @@ class Oracle:
         lib().orc_surface(self.h, float(rho_inf), _ptr(U), float(T_inf), _ptr(per),
                           _ptr(force), _ptr(heat))
         return per[:nw], force, float(heat[0])
+
+    def aero(self, x_ref=(0.0, 0.0, 0.0), S_ref=1.0, L_ref=1.0, lift_dir=(0.0, 0.0, 1.0),
+             rho_inf=None, U_inf=None):
+        """[F(3), M(3), C_D, C_L, C_m, L/D] of the current state (orc_aero)."""
+        ref = self.wl.ref
+        rho_inf = ref["rho"] if rho_inf is None else rho_inf
+        U = _c(ref["U"] if U_inf is None else U_inf, np.float64)
+        x = _c(x_ref, np.float64)
+        e = _c(lift_dir, np.float64)
+        out = np.zeros(10)
+        rc = lib().orc_aero(self.h, float(rho_inf), _ptr(U), _ptr(x), float(S_ref), float(L_ref),
+                            _ptr(e), _ptr(out))
+        if rc:
+            raise ValueError(f"orc_aero failed ({rc})")
+        return out

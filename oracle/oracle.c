@@ -1089,3 +1089,48 @@ int orc_surface(orc_ctx* c, double rho_inf, const double* U_inf, double T_inf, d
     }
     return 0;
 }
+
+/* Integrated loads and coefficients (Sec. 4, lift / drag / pitching moment); the
+ * force per unit area m_f is the wall momentum flux of Eq. cf's integrand. */
+int orc_aero(orc_ctx* c, double rho_inf, const double* U_inf, const double* x_ref,
+             double S_ref, double L_ref, const double* lift_dir, double out[10]) {
+    if (!c->prepared) return -1;
+    const double U2 = dot3(U_inf, U_inf);
+    const double q = 0.5 * rho_inf * U2;
+    if (!(q > 0.0) || !(S_ref > 0.0) || !(L_ref > 0.0)) return -2;
+    const double Um = sqrt(U2);
+    const double eD[3] = {U_inf[0] / Um, U_inf[1] / Um, U_inf[2] / Um};
+    const double a = dot3(lift_dir, eD);
+    double eL[3] = {lift_dir[0] - a * eD[0], lift_dir[1] - a * eD[1], lift_dir[2] - a * eD[2]};
+    const double nl = sqrt(dot3(eL, eL));
+    if (!(nl > 1e-12 * sqrt(dot3(lift_dir, lift_dir)))) return -2;
+    for (int d = 0; d < 3; ++d) eL[d] /= nl;
+    const double eP[3] = {eL[1] * eD[2] - eL[2] * eD[1], eL[2] * eD[0] - eL[0] * eD[2],
+                          eL[0] * eD[1] - eL[1] * eD[0]};
+    orc_step_gradient(c);
+    orc_step_faces(c);
+    double F[3] = {0.0, 0.0, 0.0}, M[3] = {0.0, 0.0, 0.0};
+    for (int64_t f = 0; f < c->F; ++f) {
+        int64_t b = c->fc[2 * f + 1];
+        if (!(b < 0 && c->bc_kind[-1 - b] == ORC_WALL)) continue;
+        const double* n = c->fn + 3 * f;
+        double m[3] = {0.0, 0.0, 0.0};
+        for (int64_t k = 0; k < c->K; ++k) {
+            const double* uk = c->u + 3 * k;
+            const double wg = c->w[k] * dot3(uk, n) * FACEV(c->face, 0, f, k);
+            for (int d = 0; d < 3; ++d) m[d] += wg * uk[d];
+        }
+        const double A = c->fa[f];
+        const double r[3] = {c->fx[3 * f] - x_ref[0], c->fx[3 * f + 1] - x_ref[1], c->fx[3 * f + 2] - x_ref[2]};
+        for (int d = 0; d < 3; ++d) F[d] += A * m[d];
+        M[0] += A * (r[1] * m[2] - r[2] * m[1]);
+        M[1] += A * (r[2] * m[0] - r[0] * m[2]);
+        M[2] += A * (r[0] * m[1] - r[1] * m[0]);
+    }
+    for (int d = 0; d < 3; ++d) { out[d] = F[d]; out[3 + d] = M[d]; }
+    out[6] = dot3(F, eD) / (q * S_ref);
+    out[7] = dot3(F, eL) / (q * S_ref);
+    out[8] = dot3(M, eP) / (q * S_ref * L_ref);
+    out[9] = out[7] / out[6];
+    return 0;
+}

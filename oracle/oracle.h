@@ -115,6 +115,15 @@ int      orc_put(orc_ctx* c, int which, const double* in);
 int64_t  orc_n_wall_faces(const orc_ctx* c);
 int      orc_surface(orc_ctx* c, double rho_inf, const double* U_inf, double T_inf,
                      double* per_face, double force[3], double* heat);
+/* Aerodynamic loads of the current state (the lift, drag, lift-to-drag and pitching
+ * moment results of Sec. 4): force F = sum_f A_f m_f and moment M = sum_f A_f
+ * (x_f - x_ref) x m_f over the wall faces, m_f = sum_k w (u.n) u g_f; with
+ * q = rho_inf |U_inf|^2 / 2, e_D = U_inf/|U_inf|, e_L = lift_dir with its e_D part
+ * removed, normalised, and e_P = e_L x e_D:
+ * out = [F(3), M(3), C_D = F.e_D/(q S), C_L = F.e_L/(q S), C_m = M.e_P/(q S L), C_L/C_D].
+ * Returns -2 for a lift direction parallel to U_inf or a non-positive S, L, q. */
+int      orc_aero(orc_ctx* c, double rho_inf, const double* U_inf, const double* x_ref,
+                  double S_ref, double L_ref, const double* lift_dir, double out[10]);
 
 /* ---- pure functions for the pins -----------------------------------------------*/
 void     orc_equilibrium(const orc_params* p, const orc_state* s, int64_t K,
