@@ -154,6 +154,23 @@ int rk_moments(rk_ctx* ctx, double* W, double* q, double* T3, int on_device);
 int rk_surface(rk_ctx* ctx, double rho_inf, const double* U_inf, double T_inf,
                double* per_wall_face, double force[3], double* heat);
 
+/* Aerodynamic loads of the current state: the lift, drag, lift-to-drag ratio and
+ * pitching moment that Sec. 4 reports for the blunted cone and the capsule (the
+ * paper gives no formulas; these are the standard definitions).  Over the wall
+ * faces, with m_f = sum_k w (u.n) u g_f the momentum flux into the wall (Eq. cf's
+ * integrand): force F = sum_f A_f m_f, moment M = sum_f A_f (x_f - x_ref) x m_f.
+ * With q = rho_inf |U_inf|^2 / 2, e_D = U_inf/|U_inf|, e_L = lift_dir minus its
+ * e_D component, normalised, and the pitch axis e_P = e_L x e_D (a positive C_m
+ * turns the upstream nose towards e_L):
+ *   out[10] = [F_x, F_y, F_z, M_x, M_y, M_z, C_D = F.e_D/(q S_ref),
+ *              C_L = F.e_L/(q S_ref), C_m = M.e_P/(q S_ref L_ref), L/D = C_L/C_D].
+ * Host pointers (U_inf, x_ref, lift_dir: 3 doubles).  RK_EINVAL for a null pointer,
+ * non-positive rho_inf, |U_inf|, S_ref or L_ref, or lift_dir parallel to U_inf;
+ * RK_ESTATE before a state is set.  Recomputes the face values of the current
+ * state (as rk_surface does); the state itself is not changed. */
+int rk_aero(rk_ctx* ctx, double rho_inf, const double* U_inf, const double* x_ref, double S_ref,
+            double L_ref, const double* lift_dir, double out[10]);
+
 /* ---- step access for verification ------------------------------------------ */
 enum {
     RK_STEP_RECON = 0,   /* LSQ gradient, limiter, reconstruction (Eq. flux_solve_phi_phi) */

@@ -298,6 +298,8 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     ctx->surf_out = cv.take<double>(8 * (size_t)(ctx->Fb + 1));
     ctx->surf_contrib = cv.take<double>(4 * (size_t)(ctx->Fb + 1));
     ctx->surf_tot = cv.take<double>(4);
+    ctx->aero_contrib = cv.take<double>(6 * (size_t)(ctx->Fb + 1));
+    ctx->aero_tot = cv.take<double>(6);
     ctx->wall_b_dev = cv.take<int>(ctx->Fb + 1);
     ctx->dbg = ctx->debug ? (void*)cv.take<T>(2 * N * Kp) : nullptr;
     return cv.off + 256;
@@ -726,6 +728,51 @@ extern "C" int rk_surface(rk_ctx* ctx, double rho_inf, const double* U_inf, doub
     if (!U_inf || !(rho_inf > 0) || !(T_inf > 0)) return fail(ctx, RK_EINVAL, "rk_surface: bad freestream");
     return ctx->prec == RK_FP64 ? surface_impl(ctx, ctx->dd, rho_inf, U_inf, T_inf, per_wall_face, force, heat)
                                 : surface_impl(ctx, ctx->df, rho_inf, U_inf, T_inf, per_wall_face, force, heat);
+}
+
+template <typename T>
+static int aero_impl(rk_ctx* ctx, rk::Dev<T>& d, const double* x_ref, double FM[6]) {
+    cudaError_t e = rk::Launch<T>::recon(d, ctx->stream, ctx->prof);
+    if (e == cudaSuccess) e = rk::Launch<T>::faces(d, ctx->stream, ctx->prof);
+    if (e == cudaSuccess)
+        e = rk::Launch<T>::aero(d, ctx->stream, ctx->wall_b_dev, ctx->nwall, x_ref, ctx->aero_contrib, ctx->aero_tot);
+    if (e != cudaSuccess) return fail(ctx, RK_ECUDA, cudaGetErrorString(e));
+    CK(cudaMemcpyAsync(ctx->pin, ctx->aero_tot, 6 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < 6; ++j) FM[j] = ctx->pin[j];
+    return RK_OK;
+}
+
+extern "C" int rk_aero(rk_ctx* ctx, double rho_inf, const double* U_inf, const double* x_ref, double S_ref,
+                       double L_ref, const double* lift_dir, double out[10]) {
+    int rc = need_bound(ctx, "rk_aero");
+    if (rc) return rc;
+    if (!ctx->have_state) return fail(ctx, RK_ESTATE, "rk_aero: set a state first");
+    if (!U_inf || !x_ref || !lift_dir || !out) return fail(ctx, RK_EINVAL, "rk_aero: null pointer");
+    const double U2 = U_inf[0] * U_inf[0] + U_inf[1] * U_inf[1] + U_inf[2] * U_inf[2];
+    const double q = 0.5 * rho_inf * U2;
+    if (!(q > 0) || !(S_ref > 0) || !(L_ref > 0))
+        return fail(ctx, RK_EINVAL, "rk_aero: rho_inf, |U_inf|, S_ref and L_ref must be positive");
+    const double Um = std::sqrt(U2);
+    const double eD[3] = {U_inf[0] / Um, U_inf[1] / Um, U_inf[2] / Um};
+    const double a = lift_dir[0] * eD[0] + lift_dir[1] * eD[1] + lift_dir[2] * eD[2];
+    double eL[3] = {lift_dir[0] - a * eD[0], lift_dir[1] - a * eD[1], lift_dir[2] - a * eD[2]};
+    const double nl = std::sqrt(eL[0] * eL[0] + eL[1] * eL[1] + eL[2] * eL[2]);
+    const double n0 = std::sqrt(lift_dir[0] * lift_dir[0] + lift_dir[1] * lift_dir[1] + lift_dir[2] * lift_dir[2]);
+    if (!(nl > 1e-12 * n0)) return fail(ctx, RK_EINVAL, "rk_aero: lift direction parallel to U_inf");
+    for (int j = 0; j < 3; ++j) eL[j] /= nl;
+    const double eP[3] = {eL[1] * eD[2] - eL[2] * eD[1], eL[2] * eD[0] - eL[0] * eD[2],
+                          eL[0] * eD[1] - eL[1] * eD[0]};
+    double FM[6];
+    rc = ctx->prec == RK_FP64 ? aero_impl(ctx, ctx->dd, x_ref, FM) : aero_impl(ctx, ctx->df, x_ref, FM);
+    if (rc) return rc;
+    for (int j = 0; j < 6; ++j) out[j] = FM[j];
+    auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    out[6] = dot(FM, eD) / (q * S_ref);
+    out[7] = dot(FM, eL) / (q * S_ref);
+    out[8] = dot(FM + 3, eP) / (q * S_ref * L_ref);
+    out[9] = out[7] / out[6];
+    return RK_OK;
 }
 
 // ---- verification access --------------------------------------------------------

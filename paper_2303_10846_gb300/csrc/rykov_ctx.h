@@ -68,6 +68,8 @@ struct rk_ctx {
     double* surf_out = nullptr;                       // [nwall][8]
     double* surf_contrib = nullptr;                   // [nwall][4]
     double* surf_tot = nullptr;                       // [4]
+    double* aero_contrib = nullptr;                   // [nwall][6]
+    double* aero_tot = nullptr;                       // [6]
     int* wall_b_dev = nullptr;
     void* dbg = nullptr;                              // [2][N][Kp] T (debug contexts)
     double* pin = nullptr;                            // pinned host: 16 doubles

@@ -1628,6 +1628,37 @@ __global__ void k_surface(Dev<T> c, const int* wall_b, int nw, double p_inf, dou
     cb[0] = c.fa[f] * wq[1]; cb[1] = c.fa[f] * wq[2]; cb[2] = c.fa[f] * wq[3]; cb[3] = c.fa[f] * wq[4];
 }
 
+// Wall loads per wall face (the lift, drag and pitching-moment integrals of Sec. 4):
+// A_f m_f and A_f (x_f - x_ref) x m_f, with m_f = sum_k w (u.n) u g_f the wall
+// momentum flux that the boundary-face kernel leaves in wallq[1..3].
+template <typename T>
+__global__ void k_aero(Dev<T> c, const int* wall_b, int nw, double x0, double y0, double z0,
+                       double* contrib) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nw) return;
+    const int b = wall_b[t];
+    const int f = c.face_bnd[b];
+    const double* wq = c.wallq + 8 * (size_t)b;
+    const double A = c.fa[f];
+    const double m[3] = {A * wq[1], A * wq[2], A * wq[3]};
+    const double r[3] = {c.fxc[f] - x0, c.fxc[c.F + f] - y0, c.fxc[2 * c.F + f] - z0};
+    double* cb = contrib + 6 * (size_t)t;
+    cb[0] = m[0]; cb[1] = m[1]; cb[2] = m[2];
+    cb[3] = r[1] * m[2] - r[2] * m[1];
+    cb[4] = r[2] * m[0] - r[0] * m[2];
+    cb[5] = r[0] * m[1] - r[1] * m[0];
+}
+
+static __global__ void __launch_bounds__(256) k_sum6(const double* contrib, int n, double* tot) {
+    __shared__ double red[6 * 8];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < n; i += 256)
+        for (int j = 0; j < 6; ++j) v[j] += contrib[6 * (size_t)i + j];
+    block_sum<6, 256>(v, red);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 6; ++j) tot[j] = v[j];
+}
+
 static __global__ void __launch_bounds__(256) k_sum4(const double* contrib, int n, double* tot) {
     __shared__ double red[4 * 8];
     double v[4] = {0, 0, 0, 0};

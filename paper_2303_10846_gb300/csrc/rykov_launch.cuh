@@ -61,6 +61,8 @@ struct Launch {
     static cudaError_t surface(const Dev<T>& d, cudaStream_t s, const int* wall_b, int nw,
                                double p_inf, double qdyn, double Umag, double* out,
                                double* contrib, double* tot);
+    static cudaError_t aero(const Dev<T>& d, cudaStream_t s, const int* wall_b, int nw,
+                            const double x_ref[3], double* contrib, double* tot);
 };
 
 extern template struct Launch<double>;

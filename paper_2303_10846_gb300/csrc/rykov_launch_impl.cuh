@@ -190,4 +190,12 @@ cudaError_t Launch<T>::surface(const Dev<T>& d, cudaStream_t s, const int* wall_
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t Launch<T>::aero(const Dev<T>& d, cudaStream_t s, const int* wall_b, int nw,
+                            const double x_ref[3], double* contrib, double* tot) {
+    if (nw) k_aero<T><<<cdiv(nw, 128), 128, 0, s>>>(d, wall_b, nw, x_ref[0], x_ref[1], x_ref[2], contrib);
+    k_sum6<<<1, 256, 0, s>>>(contrib, nw, tot);
+    return cudaGetLastError();
+}
+
 }  // namespace rk

@@ -29,7 +29,7 @@ EXPORTS = ["rk_version", "rk_create", "rk_destroy", "rk_last_error", "rk_upload_
            "rk_upload_dvs", "rk_set_params", "rk_set_bc", "rk_dims", "rk_workspace_size",
            "rk_bind_workspace", "rk_set_state_prim", "rk_set_state", "rk_get_distribution",
            "rk_implicit_iterate", "rk_residual", "rk_moments", "rk_surface", "rk_step",
-           "rk_debug_get", "rk_profile", "rk_profile_get", "rk_residual_noalloc",
+           "rk_debug_get", "rk_profile", "rk_profile_get", "rk_residual_noalloc", "rk_aero",
            "rk_noalloc_last_error", "rk_state_len", "rk_adjoint_workspace_size",
            "rk_bind_adjoint_workspace", "rk_get_state", "rk_put_state", "rk_steady_residual",
            "rk_vjp", "rk_objective", "rk_adjoint_solve", "rk_adjoint_get", "rk_debug_rows"]
@@ -81,6 +81,7 @@ def load(path: str | None = None):
         "rk_residual": ([vp, vp], C.c_int),
         "rk_moments": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "rk_surface": ([vp, dp, vp, dp, vp, vp, vp], C.c_int),
+        "rk_aero": ([vp, dp, vp, vp, dp, dp, vp, vp], C.c_int),
         "rk_step": ([vp, C.c_int], C.c_int),
         "rk_debug_get": ([vp, C.c_int, vp, i64], C.c_int),
         "rk_profile": ([vp, C.c_int], C.c_int),
@@ -260,6 +261,19 @@ class Solver:
         self._check(self.L.rk_surface(self.h, float(rho_inf), _ptr(U), float(T_inf), _ptr(per),
                                       _ptr(force), _ptr(heat)))
         return per[:self.n_wall], force, float(heat[0])
+
+    def aero(self, x_ref=(0.0, 0.0, 0.0), S_ref=1.0, L_ref=1.0, lift_dir=(0.0, 0.0, 1.0),
+             rho_inf=None, U_inf=None):
+        """[F(3), M(3), C_D, C_L, C_m, L/D] of the current state (rk_aero)."""
+        ref = self.wl.ref
+        rho_inf = ref["rho"] if rho_inf is None else rho_inf
+        U = _c(ref["U"] if U_inf is None else U_inf, np.float64)
+        x = _c(x_ref, np.float64)
+        e = _c(lift_dir, np.float64)
+        out = np.zeros(10)
+        self._check(self.L.rk_aero(self.h, float(rho_inf), _ptr(U), _ptr(x), float(S_ref),
+                                   float(L_ref), _ptr(e), _ptr(out)))
+        return out
 
     def get_distribution(self):
         torch = self.torch

@@ -145,6 +145,9 @@ def test_mixed_matches_fp64_on_the_surface_at_full_size(sphere):
     assert abs(f32 @ e - f64 @ e) <= 1e-5 * abs(f64 @ e)                                 # drag
     assert abs(h32 - h64) <= 1e-5 * np.max(np.abs(p64[:, 4])) * np.sum(sphere.mesh.face_area[
         np.nonzero(sphere.mesh.face_cell[:, 1] == -1)[0]])
+    # integrated loads: C_D, and C_L, C_m (near zero at zero incidence) on the C_D scale
+    a32, a64 = s32.aero(), s64.aero()
+    assert np.max(np.abs(a32[6:9] - a64[6:9])) <= 1e-5 * abs(a64[6])
 
 
 def test_full_size_iterations_are_bitwise_repeatable(sphere):

@@ -180,3 +180,37 @@ def test_limiter_freeze_fp64():
     W, q, _ = s.moments()
     assert _rel(W, o.get(O.BUF_W)) < TOL64
     assert _rel(q, o.get(O.BUF_Q)) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["tet", "tet_sutherland"])
+def test_aero_loads_match_oracle_fp64(name):
+    """rk_aero (force, moment, C_D, C_L, C_m, L/D) against the oracle after the same
+    iterations; an invalid lift direction is rejected."""
+    from paper_2303_10846_gb300.rykov import RK_EINVAL, RykovError
+    wl = WORKLOADS[name]()
+    o = O.Oracle(wl)
+    s = _solver(wl, debug=False)
+    o.iterate(5)
+    s.iterate(5)
+    kw = dict(x_ref=(0.1, -0.2, 0.05), S_ref=0.8, L_ref=1.5, lift_dir=(0.0, 0.3, 1.0))
+    a, b = s.aero(**kw), o.aero(**kw)
+    assert np.max(np.abs(a[:3] - b[:3])) < TOL64 * np.max(np.abs(b[:3]))
+    assert np.max(np.abs(a[3:6] - b[3:6])) < TOL64 * np.max(np.abs(b[3:6]))
+    assert np.max(np.abs(a[6:9] - b[6:9])) < TOL64 * np.max(np.abs(b[6:9]))
+    assert abs(a[9] - b[9]) < 1e-9 * abs(b[9])
+    with pytest.raises(RykovError) as ei:
+        s.aero(lift_dir=wl.ref["U"])
+    assert ei.value.code == RK_EINVAL
+
+
+def test_aero_loads_mixed_track_fp64():
+    """Mixed precision: the load coefficients stay within 1e-5 (relative to the largest)
+    of the FP64 path's after the same iterations."""
+    wl = WORKLOADS["tet"]()
+    s64 = _solver(wl, debug=False)
+    s32 = _solver(wl, "mixed", debug=False)
+    s64.iterate(5)
+    s32.iterate(5)
+    kw = dict(x_ref=(0.1, -0.2, 0.05), lift_dir=(0.0, 0.3, 1.0))
+    a, b = s32.aero(**kw), s64.aero(**kw)
+    assert np.max(np.abs(a[6:9] - b[6:9])) < 1e-5 * np.max(np.abs(b[6:9]))
