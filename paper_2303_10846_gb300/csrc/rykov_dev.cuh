@@ -37,6 +37,16 @@ constexpr int MAXF = 8;        // faces per cell
 #ifndef MICRO_LAST_MINB
 #define MICRO_LAST_MINB 4
 #endif
+#ifndef MICRO_LAST_NV
+#define MICRO_LAST_NV 2
+#endif
+#ifndef MICRO_LAST_PF
+#define MICRO_LAST_PF MICRO_PF
+#endif
+// limiter ratio in mixed mode: 1 = approximate division (__fdividef, 2 ulp)
+#ifndef RECON_FASTDIV
+#define RECON_FASTDIV 0
+#endif
 constexpr int EQN = 24;        // constants of one Rykov equilibrium (see make_eq)
 constexpr int CEQ = 28;        // per-cell record: EQN constants, 1/tau~, diagonal base
 constexpr int FST = 16;        // face state record
@@ -135,6 +145,15 @@ __device__ __forceinline__ double ex(double x) { return exp(x); }
 __device__ __forceinline__ float ex(float x) { return __expf(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+// quotient of the limiter function: exact in FP64 mode
+__device__ __forceinline__ double lim_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float lim_div(float a, float b) {
+#if RECON_FASTDIV
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
 
 // Accumulators for sums over the velocity space.  FP64 mode: plain FP64 sum.  Mixed
 // mode: Kahan-compensated FP32 sum (every operation rounded as written), combined in
@@ -314,6 +333,8 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
 }
 __device__ __forceinline__ void vload(const double* p, double (&x)[1]) { x[0] = *p; }
+__device__ __forceinline__ void vload(const float* p, float (&x)[1]) { x[0] = *p; }
+__device__ __forceinline__ void vstore(float* p, const float (&x)[1]) { *p = x[0]; }
 __device__ __forceinline__ void vstore(float* p, const float (&x)[2]) {
     *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
 }
@@ -677,13 +698,13 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
                         const T d1 = dmax[fd][e], d2 = d2hi[fd][e];
                         const T num = d1 * d1 + ep + T(2) * d1 * d2;
                         const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
-                        if (num < den) Lv = num / den;
+                        if (num < den) Lv = lim_div(num, den);
                     }
                     if (d2lo[fd][e] < T(0)) {
                         const T d1 = dmin[fd][e], d2 = d2lo[fd][e];
                         const T num = d1 * d1 + ep + T(2) * d1 * d2;
                         const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
-                        if (num < Lv * den) Lv = num / den;
+                        if (num < Lv * den) Lv = lim_div(num, den);
                     }
                     L[fd][e] = Lv;
                 }
@@ -1366,9 +1387,9 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
     constexpr bool first = FIRST, last = LAST, first_forward = FIRST;
     using R = Red<T>;
     // velocities per lane: 16-byte accesses in the middle sweeps of the mixed mode
-    constexpr int NV = sizeof(T) == 8 ? 1 : (FIRST ? MICRO_FIRST_NV : (LAST ? 2 : MICRO_MID_NV));
+    constexpr int NV = sizeof(T) == 8 ? 1 : (FIRST ? MICRO_FIRST_NV : (LAST ? MICRO_LAST_NV : MICRO_MID_NV));
     // faces whose loads are issued together
-    constexpr int PF = MICRO_PF;
+    constexpr int PF = LAST ? MICRO_LAST_PF : MICRO_PF;
     __shared__ T s_e[WPB][EQN + 2];
     __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_ok[WPB][MAXF];
     __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
