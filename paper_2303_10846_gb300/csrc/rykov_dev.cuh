@@ -35,17 +35,21 @@ constexpr int MAXF = 8;        // faces per cell
 #define MICRO_MID_MINB 5
 #endif
 #ifndef MICRO_LAST_MINB
-#define MICRO_LAST_MINB 4
+#define MICRO_LAST_MINB 2
 #endif
 #ifndef MICRO_LAST_NV
-#define MICRO_LAST_NV 2
+#define MICRO_LAST_NV 4
 #endif
 #ifndef MICRO_LAST_PF
 #define MICRO_LAST_PF MICRO_PF
 #endif
 // limiter ratio in mixed mode: 1 = approximate division (__fdividef, 2 ulp)
 #ifndef RECON_FASTDIV
-#define RECON_FASTDIV 0
+#define RECON_FASTDIV 1
+#endif
+// mixed-mode limiter: 1 = both evaluations computed and selected without branches
+#ifndef RECON_BF
+#define RECON_BF 0
 #endif
 constexpr int EQN = 24;        // constants of one Rykov equilibrium (see make_eq)
 constexpr int CEQ = 28;        // per-cell record: EQN constants, 1/tau~, diagonal base
@@ -206,6 +210,7 @@ struct Red<double> {
     static __device__ __forceinline__ V zero() { return 0.0; }
     static __device__ __forceinline__ V add(V a, V b) { return a + b; }
     static __device__ __forceinline__ V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ V shfl(V v, int l) { return __shfl_sync(0xffffffffu, v, l); }
     static __device__ __forceinline__ double to_d(V v) { return v; }
     static __device__ __forceinline__ double to_T(V v) { return v; }
     static __device__ __forceinline__ void store(double* p, V v) { *p = v; }
@@ -219,6 +224,9 @@ struct Red<float> {
     static __device__ __forceinline__ V add(V a, V b) { return ff_add(a, b); }
     static __device__ __forceinline__ V shfl_xor(V v, int o) {
         return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    }
+    static __device__ __forceinline__ V shfl(V v, int l) {
+        return FF{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
     }
     static __device__ __forceinline__ double to_d(V v) { return (double)v.hi + (double)v.lo; }
     static __device__ __forceinline__ float to_T(V v) { return __fadd_rn(v.hi, v.lo); }
@@ -239,6 +247,63 @@ __device__ __forceinline__ void warp_red(typename Red<T>::V (&v)[NV]) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[j] = Red<T>::add(v[j], Red<T>::shfl_xor(v[j], o));
     }
+}
+
+// Sum over the 32 lanes of N values whose totals are needed on lane 0 only
+// (reduce-scatter, then a gather): at the level with lane offset o every lane keeps
+// half of its slots, sending the other half to its partner (one shuffle per kept
+// slot instead of one per value), so the five levels cost ceil(N/2) + ... shuffles
+// and additions instead of 5 N; lane 0 then fetches each total from the lane that
+// holds it.  Fixed order: deterministic.  Other lanes' values are partial sums.
+#ifndef WARP_RED_SCATTER
+#define WARP_RED_SCATTER 0
+#endif
+template <typename T, int NI, int NO>
+__device__ __forceinline__ void red_level(const typename Red<T>::V (&in)[NI], typename Red<T>::V (&out)[NO],
+                                          int off) {
+    using R = Red<T>;
+    const bool upper = (threadIdx.x & off) != 0;
+#pragma unroll
+    for (int p = 0; p < NO; ++p) {
+        const typename R::V lo = in[p];
+        const typename R::V hi = (p + NO < NI) ? in[p + NO] : R::zero();
+        const typename R::V recv = R::shfl_xor(upper ? lo : hi, off);
+        out[p] = R::add(upper ? hi : lo, recv);
+    }
+}
+template <typename T, int N>
+__device__ __forceinline__ void warp_red0(typename Red<T>::V (&v)[N]) {
+    using R = Red<T>;
+    using V = typename R::V;
+    static_assert(N >= 1 && N <= 32, "warp_red0: 1..32 values");
+    constexpr int N1 = (N + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2, N4 = (N3 + 1) / 2,
+                  N5 = (N4 + 1) / 2;
+    static_assert(N5 == 1, "warp_red0: one slot per lane at the end");
+    V a1[N1], a2[N2], a3[N3], a4[N4], a5[N5];
+    red_level<T, N, N1>(v, a1, 16);
+    red_level<T, N1, N2>(a1, a2, 8);
+    red_level<T, N2, N3>(a2, a3, 4);
+    red_level<T, N3, N4>(a3, a4, 2);
+    red_level<T, N4, N5>(a4, a5, 1);
+    // value j sits on the lane whose offset bits select it at each level
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        int q = j, lane = 0;
+        if (q >= N1) { q -= N1; lane |= 16; }
+        if (q >= N2) { q -= N2; lane |= 8; }
+        if (q >= N3) { q -= N3; lane |= 4; }
+        if (q >= N4) { q -= N4; lane |= 2; }
+        if (q >= N5) { q -= N5; lane |= 1; }
+        v[j] = R::shfl(a5[0], lane);
+    }
+}
+template <typename T, int N>
+__device__ __forceinline__ void warp_red_lane0(typename Red<T>::V (&v)[N]) {
+#if WARP_RED_SCATTER
+    warp_red0<T, N>(v);
+#else
+    warp_red<T, N>(v);
+#endif
 }
 
 // Block reduction of NV values: warp butterflies, then the warps in order on thread
@@ -694,6 +759,20 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
                     const T ph0 = fd == 0 ? pg[e] : ph[e];
                     const T ep = eps2 * ph0 * ph0;
                     T Lv = T(1);
+#if RECON_BF
+                    if constexpr (sizeof(T) == 4) {
+                        // the same minimum without branches: both quotients are formed
+                        // (their denominators are positive whenever they are selected)
+                        const T a1 = dmax[fd][e], a2 = d2hi[fd][e];
+                        const T b1 = dmin[fd][e], b2 = d2lo[fd][e];
+                        const T ra = lim_div(a1 * a1 + ep + T(2) * a1 * a2, a1 * a1 + T(2) * a2 * a2 + a1 * a2 + ep);
+                        const T rb = lim_div(b1 * b1 + ep + T(2) * b1 * b2, b1 * b1 + T(2) * b2 * b2 + b1 * b2 + ep);
+                        Lv = (a2 > T(0) && ra < Lv) ? ra : Lv;
+                        Lv = (b2 < T(0) && rb < Lv) ? rb : Lv;
+                        L[fd][e] = Lv;
+                        continue;
+                    }
+#endif
                     if (d2hi[fd][e] > T(0)) {
                         const T d1 = dmax[fd][e], d2 = d2hi[fd][e];
                         const T num = d1 * d1 + ep + T(2) * d1 * d2;
@@ -827,7 +906,7 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
             v[5 + j] = R::from(t);
         }
     }
-    warp_red<T, 17>(v);
+    warp_red_lane0<T, 17>(v);
     // interface state on lane 0, in the per-velocity arithmetic type T (the moments
     // themselves are carried with compensation)
     constexpr int NB = EQN + 2;
@@ -918,7 +997,7 @@ __global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) r6[j] = R::from(m[j]);
     }
-    warp_red<T, 6>(r6);
+    warp_red_lane0<T, 6>(r6);
     if (lane == 0)
         for (int d = 0; d < 6; ++d) R::store(c.mface + (size_t)f * 6 + d, r6[d]);
 }
@@ -1532,7 +1611,7 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
         typename R::V v[12];
 #pragma unroll
         for (int j = 0; j < 12; ++j) v[j] = R::from(a[j]);
-        warp_red<T, 12>(v);
+        warp_red_lane0<T, 12>(v);
         if (lane == 0)
             for (int j = 0; j < 12; ++j) c.S[(size_t)i * 12 + j] = R::to_d(v[j]);
     }
