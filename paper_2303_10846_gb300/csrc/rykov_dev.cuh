@@ -49,7 +49,7 @@ constexpr int MAXF = 8;        // faces per cell
 #endif
 // mixed-mode limiter: 1 = both evaluations computed and selected without branches
 #ifndef RECON_BF
-#define RECON_BF 0
+#define RECON_BF 1
 #endif
 constexpr int EQN = 24;        // constants of one Rykov equilibrium (see make_eq)
 constexpr int CEQ = 28;        // per-cell record: EQN constants, 1/tau~, diagonal base
@@ -153,7 +153,10 @@ __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double lim_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float lim_div(float a, float b) {
 #if RECON_FASTDIV
-    return __fdividef(a, b);
+    // the approximate quotient takes the reciprocal of b, which overflows (or is
+    // flushed) for b below ~1e-38: there, as in the distribution tails where the
+    // differences are that small, the exact division
+    return b > 1e-30f ? __fdividef(a, b) : a / b;
 #else
     return a / b;
 #endif
@@ -256,7 +259,7 @@ __device__ __forceinline__ void warp_red(typename Red<T>::V (&v)[NV]) {
 // and additions instead of 5 N; lane 0 then fetches each total from the lane that
 // holds it.  Fixed order: deterministic.  Other lanes' values are partial sums.
 #ifndef WARP_RED_SCATTER
-#define WARP_RED_SCATTER 0
+#define WARP_RED_SCATTER 1
 #endif
 template <typename T, int NI, int NO>
 __device__ __forceinline__ void red_level(const typename Red<T>::V (&in)[NI], typename Red<T>::V (&out)[NO],
@@ -1460,6 +1463,72 @@ __global__ void __launch_bounds__(WPB * 32) k_micro_flux(Dev<T> c) {
 // FIRST (forms Res; the first sweep is the forward one) and LAST (update and Step-6
 // sums) are separate instantiations, so that the middle sweeps carry neither the
 // face reads nor the twelve accumulators
+// The part of one micro point update that follows the face loop (shared by both
+// sweep kernels): Res (first sweep: from phi and the micro flux F, written in place of
+// F), the increment dphi = (Res - offdiag) / D, and in the last sweep phi^{n+1} and
+// the lane's Step-6 sums.  r0 holds F (first sweep) or Res (later sweeps).
+template <typename T, int NV, bool FIRST, bool LAST>
+__device__ __forceinline__ void micro_tail(const Dev<T>& c, const T* e, T itau, size_t oi, size_t NK, int k0,
+                                           const T (&ux)[NV], const T (&uy)[NV], const T (&uz)[NV],
+                                           const T (&D)[NV], const T (&og)[NV], const T (&oh)[NV],
+                                           const T (&pg)[NV], const T (&ph)[NV], const T (&r0g)[NV],
+                                           const T (&r0h)[NV], Acc<T> (&a)[12]) {
+    constexpr bool first = FIRST, last = LAST;
+    T G[NV], H[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        G[v] = H[v] = T(0);
+        if (first || last) eval_eq(e, ux[v], uy[v], uz[v], G[v], H[v]);
+    }
+    T rg[NV], rh[NV];
+    if (first) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            rg[v] = (G[v] - pg[v]) * itau - r0g[v];
+            rh[v] = (H[v] - ph[v]) * itau - r0h[v];
+        }
+        vstore(c.res + oi + k0, rg);
+        vstore(c.res + NK + oi + k0, rh);
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { rg[v] = r0g[v]; rh[v] = r0h[v]; }
+    }
+    T xg[NV], xh[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const T iD = rcp(D[v]);
+        xg[v] = (rg[v] - og[v]) * iD;
+        xh[v] = (rh[v] - oh[v]) * iD;
+    }
+    vstore(c.dphi + oi + k0, xg);
+    vstore(c.dphi + NK + oi + k0, xh);
+    if (last) {
+        T g1[NV], h1[NV], wv[NV];
+        vload(c.wT + k0, wv);
+        // the lane's NV terms are summed plainly, then added with compensation
+        T t[12];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            g1[v] = pg[v] + xg[v];
+            h1[v] = ph[v] + xh[v];
+            const T Dg = g1[v] - G[v], Dh = h1[v] - H[v];
+            const T cx = ux[v] - e[0], cy = uy[v] - e[1], cz = uz[v] - e[2];
+            const T c2 = cx * cx + cy * cy + cz * cz;
+            const T wg = wv[v] * Dg, wh = wv[v] * Dh;
+            const T wgc = wg * c2;
+            const T tv[12] = {wg, wg * ux[v], wg * uy[v], wg * uz[v],
+                              T(0.5) * (ux[v] * ux[v] + uy[v] * uy[v] + uz[v] * uz[v]) * wg + wh, wh,
+                              wgc * cx, wgc * cy, wgc * cz, wh * cx, wh * cy, wh * cz};
+#pragma unroll
+            for (int j = 0; j < 12; ++j) t[j] = v == 0 ? tv[j] : t[j] + tv[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 12; ++j) a[j].add(t[j]);
+        vstore(c.phi + oi + k0, g1);
+        vstore(c.phi + NK + oi + k0, h1);
+    }
+}
+
 template <typename T, int WPB, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_LAST_MINB : (FIRST ? MICRO_FIRST_MINB : MICRO_MID_MINB)))
     k_micro_sweep(Dev<T> c, const int* cells, int ncells, int colour) {
@@ -1500,9 +1569,9 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
         vload(c.uT + k0, ux);
         vload(c.uT + c.Kp + k0, uy);
         vload(c.uT + 2 * c.Kp + k0, uz);
-        T D[NV], og[NV], oh[NV], Fg[NV], Fh[NV];
+        T D[NV], og[NV], oh[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) { D[q] = base; og[q] = oh[q] = Fg[q] = Fh[q] = T(0); }
+        for (int q = 0; q < NV; ++q) { D[q] = base; og[q] = oh[q] = T(0); }
         // faces in groups of PF: all loads of a group are issued before its arithmetic,
         // so that PF neighbour rows are in flight per thread (the accumulation order
         // over the faces is unchanged)
@@ -1546,67 +1615,174 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
                 }
             }
         }
-        T G[NV], H[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            G[v] = H[v] = T(0);
-            if (first || last) eval_eq(e, ux[v], uy[v], uz[v], G[v], H[v]);
-        }
-        T rg[NV], rh[NV], pg[NV], ph[NV];
+        T pg[NV], ph[NV], r0g[NV], r0h[NV];
         if (first || last) {
             vload(c.phi + oi + k0, pg);
             vload(c.phi + NK + oi + k0, ph);
         }
-        if (first) {
-            // res holds the micro flux F (k_micro_flux); Res replaces it in place
-            vload(c.res + oi + k0, Fg);
-            vload(c.res + NK + oi + k0, Fh);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                rg[v] = (G[v] - pg[v]) * itau - Fg[v];
-                rh[v] = (H[v] - ph[v]) * itau - Fh[v];
-            }
-            vstore(c.res + oi + k0, rg);
-            vstore(c.res + NK + oi + k0, rh);
-        } else {
-            vload(c.res + oi + k0, rg);
-            vload(c.res + NK + oi + k0, rh);
-        }
-        T xg[NV], xh[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const T iD = rcp(D[v]);
-            xg[v] = (rg[v] - og[v]) * iD;
-            xh[v] = (rh[v] - oh[v]) * iD;
-        }
-        vstore(c.dphi + oi + k0, xg);
-        vstore(c.dphi + NK + oi + k0, xh);
-        if (last) {
-            T g1[NV], h1[NV], wv[NV];
-            vload(c.wT + k0, wv);
-            // the lane's NV terms are summed plainly, then added with compensation
-            T t[12];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                g1[v] = pg[v] + xg[v];
-                h1[v] = ph[v] + xh[v];
-                const T Dg = g1[v] - G[v], Dh = h1[v] - H[v];
-                const T cx = ux[v] - e[0], cy = uy[v] - e[1], cz = uz[v] - e[2];
-                const T c2 = cx * cx + cy * cy + cz * cz;
-                const T wg = wv[v] * Dg, wh = wv[v] * Dh;
-                const T wgc = wg * c2;
-                const T tv[12] = {wg, wg * ux[v], wg * uy[v], wg * uz[v],
-                                  T(0.5) * (ux[v] * ux[v] + uy[v] * uy[v] + uz[v] * uz[v]) * wg + wh, wh,
-                                  wgc * cx, wgc * cy, wgc * cz, wh * cx, wh * cy, wh * cz};
-#pragma unroll
-                for (int j = 0; j < 12; ++j) t[j] = v == 0 ? tv[j] : t[j] + tv[j];
-            }
-#pragma unroll
-            for (int j = 0; j < 12; ++j) a[j].add(t[j]);
-            vstore(c.phi + oi + k0, g1);
-            vstore(c.phi + NK + oi + k0, h1);
-        }
+        // F in the first sweep (k_micro_flux), Res in the later ones
+        vload(c.res + oi + k0, r0g);
+        vload(c.res + NK + oi + k0, r0h);
+        micro_tail<T, NV, FIRST, LAST>(c, e, itau, oi, NK, k0, ux, uy, uz, D, og, oh, pg, ph, r0g, r0h, a);
     }
+    if (last) {
+        typename R::V v[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) v[j] = R::from(a[j]);
+        warp_red_lane0<T, 12>(v);
+        if (lane == 0)
+            for (int j = 0; j < 12; ++j) c.S[(size_t)i * 12 + j] = R::to_d(v[j]);
+    }
+}
+
+// Asynchronous copies global -> shared (cp.async; completion per thread, counted by
+// commit groups).  16-byte copies bypass L1 (.cg); smaller ones go through it (.ca).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The micro point update of k_micro_sweep with its row loads staged through shared
+// memory: while a warp computes one chunk of 32 x NV velocities, the rows of the next
+// chunk (the neighbours' dphi at the faces that have an inflow velocity in the lane's
+// group, the cell's own phi and F/Res) are already in flight as asynchronous copies,
+// double-buffered, so the loads do not wait in registers.  Every lane copies and
+// reads back only its own NV values, so the copies need no barrier beyond the
+// thread's own wait.  Same arithmetic in the same order as k_micro_sweep.
+// Dynamic shared memory: WPB x 2 stages x (2 maxs + 4) rows x 32 lanes x NV values.
+#ifndef MICRO_ST_WPB
+#define MICRO_ST_WPB 4
+#endif
+template <typename T, bool FIRST, bool LAST>
+__host__ __device__ constexpr int micro_nv() {
+    return sizeof(T) == 8 ? 1 : (FIRST ? MICRO_FIRST_NV : (LAST ? MICRO_LAST_NV : MICRO_MID_NV));
+}
+template <typename T, int WPB, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(WPB * 32)
+    k_micro_sweep_st(Dev<T> c, const int* cells, int ncells, int colour, int maxs) {
+    constexpr bool first = FIRST, last = LAST, first_forward = FIRST;
+    using R = Red<T>;
+    constexpr int NV = micro_nv<T, FIRST, LAST>();
+    constexpr int BY = NV * (int)sizeof(T);
+    extern __shared__ __align__(16) unsigned char st_raw[];
+    __shared__ T s_e[WPB][EQN + 2];
+    __shared__ int s_nbr[WPB][MAXF], s_ok[WPB][MAXF];
+    __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * WPB + w;
+    if (t >= ncells) return;                      // whole warp: no block barriers below
+    const int i = cells[t];
+    const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
+    if (lane < EQN + 2) s_e[w][lane] = (T)c.ceq[(size_t)i * CEQ + lane];
+    if (lane < ns) {
+        const int m = s0 + lane;
+        s_nbr[w][lane] = c.slot_nbr[m];
+        s_ok[w][lane] = (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour);
+        const T sg = c.slot_left[m] ? T(1) : T(-1);
+        s_n[w][0][lane] = sg * c.slot_nT[m];
+        s_n[w][1][lane] = sg * c.slot_nT[c.nnz + m];
+        s_n[w][2][lane] = sg * c.slot_nT[2 * c.nnz + m];
+        s_AV[w][lane] = c.slot_AVT[m];
+    }
+    __syncwarp();
+    const T* e = s_e[w];
+    const T itau = e[EQN - 1], base = e[EQN];
+    const size_t NK = (size_t)c.N * c.Kp;
+    const size_t oi = (size_t)i * c.Kp;
+    const int nrow = 2 * maxs + 4;                // rows per stage: 2 per face, phi g/h, F|Res g/h
+    T* buf = reinterpret_cast<T*>(st_raw) + (size_t)w * 2 * nrow * 32 * NV + (size_t)lane * NV;
+    // this lane's slot of row r in stage st
+    auto slot = [&](int st, int r) { return buf + (size_t)(st * nrow + r) * 32 * NV; };
+    const int nch = (c.K + 32 * NV - 1) / (32 * NV);
+    // issue the copies of chunk ch into stage st; returns the faces copied (bit mask)
+    auto prefetch = [&](int ch, int st) -> unsigned {
+        const int k0 = ch * 32 * NV + NV * lane;
+        unsigned mk = 0u;
+        if (k0 < c.K) {
+            T ux[NV], uy[NV], uz[NV];
+            vload(c.uT + k0, ux);
+            vload(c.uT + c.Kp + k0, uy);
+            vload(c.uT + 2 * c.Kp + k0, uz);
+#pragma unroll 1
+            for (int q = 0; q < ns; ++q) {
+                if (!s_ok[w][q]) continue;
+                const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+                bool neg = false;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) neg = neg || !(dot_split(ux[v], uy[v], uz[v], nx, ny, nz) > T(0));
+                if (neg) {
+                    const size_t oj = (size_t)s_nbr[w][q] * c.Kp + k0;
+                    cp_async<BY>(slot(st, 2 * q), c.dphi + oj);
+                    cp_async<BY>(slot(st, 2 * q + 1), c.dphi + NK + oj);
+                    mk |= 1u << q;
+                }
+            }
+            if (first || last) {
+                cp_async<BY>(slot(st, 2 * maxs), c.phi + oi + k0);
+                cp_async<BY>(slot(st, 2 * maxs + 1), c.phi + NK + oi + k0);
+            }
+            cp_async<BY>(slot(st, 2 * maxs + 2), c.res + oi + k0);
+            cp_async<BY>(slot(st, 2 * maxs + 3), c.res + NK + oi + k0);
+        }
+        cp_async_commit();
+        return mk;
+    };
+    Acc<T> a[12];
+    unsigned m_next = prefetch(0, 0);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int st = ch & 1;
+        const unsigned m_cur = m_next;
+        if (ch + 1 < nch) m_next = prefetch(ch + 1, st ^ 1);
+        else cp_async_commit();                   // an empty group keeps the count
+        cp_async_wait<1>();                       // this thread's copies of chunk ch are done
+        const int k0 = ch * 32 * NV + NV * lane;
+        if (k0 >= c.K) continue;
+        T ux[NV], uy[NV], uz[NV];
+        vload(c.uT + k0, ux);
+        vload(c.uT + c.Kp + k0, uy);
+        vload(c.uT + 2 * c.Kp + k0, uz);
+        T D[NV], og[NV], oh[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { D[q] = base; og[q] = oh[q] = T(0); }
+#pragma unroll 1
+        for (int q = 0; q < ns; ++q) {
+            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+            T un[NV], dg[NV], dh[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) un[v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
+            const bool okq = (m_cur >> q) & 1u;
+            if (okq) {
+                vload(slot(st, 2 * q), dg);
+                vload(slot(st, 2 * q + 1), dh);
+            }
+            const T AV = s_AV[w][q];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if (un[v] > T(0)) {
+                    D[v] += AV * un[v];
+                } else if (okq) {
+                    og[v] += AV * un[v] * dg[v];
+                    oh[v] += AV * un[v] * dh[v];
+                }
+            }
+        }
+        T pg[NV], ph[NV], r0g[NV], r0h[NV];
+        if (first || last) {
+            vload(slot(st, 2 * maxs), pg);
+            vload(slot(st, 2 * maxs + 1), ph);
+        }
+        vload(slot(st, 2 * maxs + 2), r0g);
+        vload(slot(st, 2 * maxs + 3), r0h);
+        micro_tail<T, NV, FIRST, LAST>(c, e, itau, oi, NK, k0, ux, uy, uz, D, og, oh, pg, ph, r0g, r0h, a);
+    }
+    cp_async_wait<0>();
     if (last) {
         typename R::V v[12];
 #pragma unroll

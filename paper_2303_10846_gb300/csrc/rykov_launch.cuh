@@ -37,6 +37,8 @@ struct Sched {
     const int* col_cell;            // device: cells grouped by colour
     std::vector<int> col_off;       // host: colour offsets (C+1)
     int coop_grid = 0;              // blocks of the cooperative macro solve (0: per-colour launches)
+    int maxs = 0;                   // most faces of one cell
+    bool staged = false;            // micro sweeps with staged (asynchronous) row loads
 };
 
 template <typename T>
@@ -55,6 +57,9 @@ struct Launch {
                              Prof& pf);
     static cudaError_t micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,
                              Prof& pf);
+    // shared memory of the staged micro sweeps for a mesh with at most maxs faces per
+    // cell (0 if it exceeds the device limit); sets the kernels' attribute
+    static size_t micro_staged_smem(int maxs);
     static cudaError_t debug_micro_flux(const Dev<T>& d, cudaStream_t s, T* out);
     static cudaError_t temps(const Dev<T>& d, cudaStream_t s, double* out);
     static int coop_blocks_per_sm();

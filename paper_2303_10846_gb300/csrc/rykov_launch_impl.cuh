@@ -130,6 +130,15 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
     return cudaGetLastError();
 }
 
+// dynamic shared memory of one block of the staged micro sweep
+template <typename T>
+struct StBytes {
+    template <bool FIRST, bool LAST>
+    static size_t get(int maxs) {
+        return (size_t)MICRO_ST_WPB * 2 * (2 * maxs + 4) * 32 * micro_nv<T, FIRST, LAST>() * sizeof(T);
+    }
+};
+
 template <typename T>
 cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_micro,
                              Prof& pf) {
@@ -144,11 +153,23 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             // the first sweep forms Res for every cell of this colour; the last
             // sweep applies the update and the Step-6 sums
             pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
-            const dim3 g(cdiv(n, MICRO_WPB)), b(MICRO_WPB * 32);
             const int* cl = sc.col_cell + lo;
-            if (sw == 0) k_micro_sweep<T, MICRO_WPB, true, false><<<g, b, 0, s>>>(d, cl, n, col);
-            else if (sw == nsw - 1) k_micro_sweep<T, MICRO_WPB, false, true><<<g, b, 0, s>>>(d, cl, n, col);
-            else k_micro_sweep<T, MICRO_WPB, false, false><<<g, b, 0, s>>>(d, cl, n, col);
+            if (sc.staged) {
+                constexpr int W = MICRO_ST_WPB;
+                const dim3 g(cdiv(n, W)), b(W * 32);
+                const int mx = sc.maxs;
+                if (sw == 0)
+                    k_micro_sweep_st<T, W, true, false><<<g, b, StBytes<T>::template get<true, false>(mx), s>>>(d, cl, n, col, mx);
+                else if (sw == nsw - 1)
+                    k_micro_sweep_st<T, W, false, true><<<g, b, StBytes<T>::template get<false, true>(mx), s>>>(d, cl, n, col, mx);
+                else
+                    k_micro_sweep_st<T, W, false, false><<<g, b, StBytes<T>::template get<false, false>(mx), s>>>(d, cl, n, col, mx);
+            } else {
+                const dim3 g(cdiv(n, MICRO_WPB)), b(MICRO_WPB * 32);
+                if (sw == 0) k_micro_sweep<T, MICRO_WPB, true, false><<<g, b, 0, s>>>(d, cl, n, col);
+                else if (sw == nsw - 1) k_micro_sweep<T, MICRO_WPB, false, true><<<g, b, 0, s>>>(d, cl, n, col);
+                else k_micro_sweep<T, MICRO_WPB, false, false><<<g, b, 0, s>>>(d, cl, n, col);
+            }
             pf.end(s);
             pf.launches += 1;
         }
@@ -159,6 +180,27 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
     pf.end(s);
     pf.launches += 2;
     return cudaGetLastError();
+}
+
+template <typename T>
+size_t Launch<T>::micro_staged_smem(int maxs) {
+    const size_t need = StBytes<T>::template get<true, false>(maxs) > StBytes<T>::template get<false, true>(maxs)
+                            ? StBytes<T>::template get<true, false>(maxs) : StBytes<T>::template get<false, true>(maxs);
+    const size_t need2 = need > StBytes<T>::template get<false, false>(maxs) ? need : StBytes<T>::template get<false, false>(maxs);
+    int dev = 0, lim = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    // the kernels' static shared memory comes on top of the dynamic part
+    if (need2 + 4096 > (size_t)lim) return 0;
+    constexpr int W = MICRO_ST_WPB;
+    if (cudaFuncSetAttribute(k_micro_sweep_st<T, W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)StBytes<T>::template get<true, false>(maxs)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_micro_sweep_st<T, W, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)StBytes<T>::template get<false, true>(maxs)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_micro_sweep_st<T, W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)StBytes<T>::template get<false, false>(maxs)) != cudaSuccess)
+        return 0;
+    return need2;
 }
 
 template <typename T>

@@ -171,3 +171,26 @@ def test_cooperative_macro_solve_is_bitwise_identical_at_full_size(sphere, monke
     b.iterate(15)
     Wb, qb, _ = b.moments()
     assert np.array_equal(Wa, Wb) and np.array_equal(qa, qb)
+
+
+def test_staged_micro_sweeps_are_bitwise_identical_at_full_size(sphere, monkeypatch):
+    """Staged and direct row loads in the micro sweeps give the same iterates on the
+    full sphere (mixed precision, the bench configuration)."""
+    out = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("RYKOV_STAGED", flag)
+        s = _solver(sphere, "mixed")
+        s.iterate(15)
+        out.append(s.moments()[:2])
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_long_mixed_run_stays_finite(sphere):
+    """300 mixed-precision iterations from the initial field (past the point where the
+    distribution tails reach the FP32 subnormal range): the residual stays finite and
+    falls below 1e-4."""
+    s = _solver(sphere, "mixed")
+    rc, n, res = s.iterate(300)
+    assert rc == 0 and n == 300
+    assert np.all(np.isfinite(res)) and np.max(res) < 1e-4
