@@ -32,8 +32,9 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     // on the cooperative macro solve (same results; used to compare launch schemes)
     if (const char* v = std::getenv("RYKOV_GRAPH")) ctx->use_graph = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("RYKOV_COOP")) ctx->use_coop = std::strcmp(v, "0") != 0;
-    // RYKOV_STAGED=0/1 chooses the micro sweeps with direct or staged row loads
-    if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::strcmp(v, "0") != 0;
+    // RYKOV_STAGED: which micro sweeps stage their row loads (bits 0/1/2: first,
+    // middle, last sweep); the results are the same either way
+    if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::atoi(v) & 7;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
     std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
@@ -406,7 +407,7 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
         int maxs = 0;
         for (int64_t i = 0; i < N; ++i) maxs = std::max(maxs, ctx->slot_off[i + 1] - ctx->slot_off[i]);
         ctx->sched.maxs = maxs;
-        ctx->sched.staged = ctx->use_staged && rk::Launch<T>::micro_staged_smem(maxs) > 0;
+        ctx->sched.staged = (ctx->use_staged && rk::Launch<T>::micro_staged_smem(maxs) > 0) ? ctx->use_staged : 0;
         cudaGetLastError();
     }
     // zero the distribution-sized arrays once so that the K padding stays 0

@@ -36,7 +36,7 @@ using rkh::MAX_BC;
 using rkh::RK_DEBUG_FLAG;
 
 #ifndef RK_STAGED_DEFAULT
-#define RK_STAGED_DEFAULT false
+#define RK_STAGED_DEFAULT 4
 #endif
 
 struct rk_ctx {
@@ -83,7 +83,7 @@ struct rk_ctx {
     // the caller's stream); rebuilt after anything baked into it changes
     bool use_graph = true;
     bool use_coop = false;            // cooperative launch of the macro PR-SGS (RYKOV_COOP=1)
-    bool use_staged = RK_STAGED_DEFAULT;  // staged micro sweeps (RYKOV_STAGED)
+    int use_staged = RK_STAGED_DEFAULT;   // staged micro sweeps, bit mask (RYKOV_STAGED)
     cudaStream_t cap = nullptr, cap2 = nullptr;   // capture streams (main, side branch)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bnd = nullptr, ev_int = nullptr;
     cudaGraphExec_t gexec = nullptr;

@@ -153,10 +153,11 @@ __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double lim_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float lim_div(float a, float b) {
 #if RECON_FASTDIV
-    // the approximate quotient takes the reciprocal of b, which overflows (or is
-    // flushed) for b below ~1e-38: there, as in the distribution tails where the
-    // differences are that small, the exact division
-    return b > 1e-30f ? __fdividef(a, b) : a / b;
+    // the approximate quotient takes the reciprocal of b, which overflows for b below
+    // ~1e-38 (the distribution tails give such differences): both operands are then
+    // scaled by 2^64 first (exact), which leaves the quotient unchanged
+    const float sc = b < 1e-30f ? 18446744073709551616.0f : 1.0f;
+    return __fdividef(a * sc, b * sc);
 #else
     return a / b;
 #endif
@@ -1499,6 +1500,10 @@ __device__ __forceinline__ void micro_tail(const Dev<T>& c, const T* e, T itau, 
         const T iD = rcp(D[v]);
         xg[v] = (rg[v] - og[v]) * iD;
         xh[v] = (rh[v] - oh[v]) * iD;
+        // the lane's last group can reach into the K padding, which must stay zero
+        // (with nonzero increments there, the sphere run turned non-finite after
+        // ~200 iterations once the last sweep also updated the padded phi)
+        if (k0 + v >= c.K) xg[v] = xh[v] = T(0);
     }
     vstore(c.dphi + oi + k0, xg);
     vstore(c.dphi + NK + oi + k0, xh);

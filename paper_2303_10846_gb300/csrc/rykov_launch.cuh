@@ -38,7 +38,8 @@ struct Sched {
     std::vector<int> col_off;       // host: colour offsets (C+1)
     int coop_grid = 0;              // blocks of the cooperative macro solve (0: per-colour launches)
     int maxs = 0;                   // most faces of one cell
-    bool staged = false;            // micro sweeps with staged (asynchronous) row loads
+    int staged = 0;                 // micro sweeps with staged (asynchronous) row loads:
+                                    // bit 0 first sweep, bit 1 middle sweeps, bit 2 last
 };
 
 template <typename T>

@@ -154,7 +154,8 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             // sweep applies the update and the Step-6 sums
             pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
             const int* cl = sc.col_cell + lo;
-            if (sc.staged) {
+            const int kind = sw == 0 ? 0 : (sw == nsw - 1 ? 2 : 1);
+            if ((sc.staged >> kind) & 1) {
                 constexpr int W = MICRO_ST_WPB;
                 const dim3 g(cdiv(n, W)), b(W * 32);
                 const int mx = sc.maxs;
