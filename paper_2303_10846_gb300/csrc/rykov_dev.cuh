@@ -673,26 +673,33 @@ __global__ void k_set_state(Dev<T> c, const double* prim, const double* qin) {
 // cell, velocities strided over the block; the cell's face data staged in shared
 // memory.
 // ------------------------------------------------------------------------------------
+// per-slot records of the reconstruction, one 16-byte (mixed) or 32-byte (FP64)
+// shared-memory load each
+template <typename T>
+struct alignas(4 * sizeof(T)) Q4 {
+    T x, y, z, w;
+};
+#ifndef RECON_MINB
+#define RECON_MINB 3
+#endif
 template <typename T, int WPB>
-__global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
+__global__ void __launch_bounds__(WPB * 32, RECON_MINB) k_recon(Dev<T> c) {
     constexpr int NV = VW<T>::N;
-    __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_left[WPB][MAXF];
-    __shared__ T s_lsq[WPB][3][MAXF], s_d[WPB][3][MAXF], s_n[WPB][3][MAXF], s_s[WPB][MAXF];
+    __shared__ Q4<T> s_A[WPB][MAXF];              // LSQ weight vector, s_ij
+    __shared__ Q4<T> s_B[WPB][MAXF];              // x_f - x_i, s_ij
+    __shared__ Q4<T> s_C[WPB][MAXF];              // face normal
+    __shared__ int4 s_I[WPB][MAXF];               // neighbour, face, left side
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * WPB + w;
     if (i >= c.N) return;                         // whole warp
     const int s0 = c.slot_off[i], ns = c.slot_off[i + 1] - s0;
     if (lane < ns) {
         const int m = s0 + lane;
-        s_face[w][lane] = c.slot_face[m];
-        s_nbr[w][lane] = c.slot_nbr[m];
-        s_left[w][lane] = c.slot_left[m];
-        s_s[w][lane] = c.slot_sT[m];
-        for (int r = 0; r < 3; ++r) {
-            s_lsq[w][r][lane] = c.slot_lsqT[r * c.nnz + m];
-            s_d[w][r][lane] = c.slot_dT[r * c.nnz + m];
-            s_n[w][r][lane] = c.slot_nT[r * c.nnz + m];
-        }
+        const T sq = c.slot_sT[m];
+        s_A[w][lane] = Q4<T>{c.slot_lsqT[m], c.slot_lsqT[c.nnz + m], c.slot_lsqT[2 * c.nnz + m], sq};
+        s_B[w][lane] = Q4<T>{c.slot_dT[m], c.slot_dT[c.nnz + m], c.slot_dT[2 * c.nnz + m], sq};
+        s_C[w][lane] = Q4<T>{c.slot_nT[m], c.slot_nT[c.nnz + m], c.slot_nT[2 * c.nnz + m], T(0)};
+        s_I[w][lane] = make_int4(c.slot_nbr[m], c.slot_face[m], c.slot_left[m], 0);
     }
     __syncwarp();
     const T eps2 = (T)c.eps2[i];
@@ -700,133 +707,139 @@ __global__ void __launch_bounds__(WPB * 32, 3) k_recon(Dev<T> c) {
     const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
     const T* phg = c.phi + (size_t)i * c.Kp;
     const T* phh = c.phi + NK + (size_t)i * c.Kp;
-    for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
-        T pg[NV], ph[NV];
-        vload(phg + k0, pg);
-        vload(phh + k0, ph);
-        T g[2][3][NV], dmax[2][NV], dmin[2][NV];
-#pragma unroll
-        for (int e = 0; e < NV; ++e)
-            for (int fd = 0; fd < 2; ++fd) {
-                g[fd][0][e] = g[fd][1][e] = g[fd][2][e] = T(0);
-                dmax[fd][e] = dmin[fd][e] = T(0);
-            }
+    // the velocity loop; the face loops are not unrolled (a fully unrolled four-face
+    // variant measured slower: more registers, fewer resident warps)
+    auto body = [&]() {
+        auto for_faces = [&](auto&& f) {
 #pragma unroll 1
-        for (int q = 0; q < ns; ++q) {
-            const int j = s_nbr[w][q];
-            if (j < 0) continue;
-            T xg[NV], xh[NV];
-            vload(c.phi + (size_t)j * c.Kp + k0, xg);
-            vload(c.phi + NK + (size_t)j * c.Kp + k0, xh);
-            const T lx = s_lsq[w][0][q], ly = s_lsq[w][1][q], lz = s_lsq[w][2][q];
+            for (int q = 0; q < ns; ++q) f(q);
+        };
+        for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+            T pg[NV], ph[NV];
+            vload(phg + k0, pg);
+            vload(phh + k0, ph);
+            T g[2][3][NV], dmax[2][NV], dmin[2][NV];
 #pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                const T dg = xg[e] - pg[e], dh = xh[e] - ph[e];
-                g[0][0][e] += lx * dg; g[0][1][e] += ly * dg; g[0][2][e] += lz * dg;
-                g[1][0][e] += lx * dh; g[1][1][e] += ly * dh; g[1][2][e] += lz * dh;
-                dmax[0][e] = dg > dmax[0][e] ? dg : dmax[0][e]; dmin[0][e] = dg < dmin[0][e] ? dg : dmin[0][e];
-                dmax[1][e] = dh > dmax[1][e] ? dh : dmax[1][e]; dmin[1][e] = dh < dmin[1][e] ? dh : dmin[1][e];
-            }
-        }
-        T L[2][NV];
+            for (int e = 0; e < NV; ++e)
+                for (int fd = 0; fd < 2; ++fd) {
+                    g[fd][0][e] = g[fd][1][e] = g[fd][2][e] = T(0);
+                    dmax[fd][e] = dmin[fd][e] = T(0);
+                }
+            for_faces([&](int q) {
+                const int j = s_I[w][q].x;
+                if (j < 0) return;
+                T xg[NV], xh[NV];
+                vload(c.phi + (size_t)j * c.Kp + k0, xg);
+                vload(c.phi + NK + (size_t)j * c.Kp + k0, xh);
+                const Q4<T> A = s_A[w][q];
 #pragma unroll
-        for (int e = 0; e < NV; ++e) L[0][e] = L[1][e] = (limiter == 2) ? T(0) : T(1);
-        if (limiter == 3) {
-            // frozen limiter values
-            vload(c.lstore + (size_t)i * c.Kp + k0, L[0]);
-            vload(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
-        } else if (limiter == 1 || limiter == 4) {
-            // min over faces of Venkatakrishnan's psi(d1, d2), capped at 1, threshold
-            // eps^2 phi_i^2 relative to the cell value (readings).  psi < 1 needs
-            // y = d2/d1 > 1/2, where psi decreases in y; so the minimum over the faces
-            // with d2 > 0 is psi(Delta_max, max d2) and over d2 < 0 psi(Delta_min, min d2):
-            // two evaluations instead of one per face (the same value up to rounding)
-            T d2hi[2][NV], d2lo[2][NV];
+                for (int e = 0; e < NV; ++e) {
+                    const T dg = xg[e] - pg[e], dh = xh[e] - ph[e];
+                    g[0][0][e] += A.x * dg; g[0][1][e] += A.y * dg; g[0][2][e] += A.z * dg;
+                    g[1][0][e] += A.x * dh; g[1][1][e] += A.y * dh; g[1][2][e] += A.z * dh;
+                    dmax[0][e] = dg > dmax[0][e] ? dg : dmax[0][e]; dmin[0][e] = dg < dmin[0][e] ? dg : dmin[0][e];
+                    dmax[1][e] = dh > dmax[1][e] ? dh : dmax[1][e]; dmin[1][e] = dh < dmin[1][e] ? dh : dmin[1][e];
+                }
+            });
+            T L[2][NV];
 #pragma unroll
-            for (int e = 0; e < NV; ++e) d2hi[0][e] = d2hi[1][e] = d2lo[0][e] = d2lo[1][e] = T(0);
-#pragma unroll 1
-            for (int q = 0; q < ns; ++q) {
-                const T dx = s_d[w][0][q], dy = s_d[w][1][q], dz = s_d[w][2][q];
+            for (int e = 0; e < NV; ++e) L[0][e] = L[1][e] = (limiter == 2) ? T(0) : T(1);
+            if (limiter == 3) {
+                // frozen limiter values
+                vload(c.lstore + (size_t)i * c.Kp + k0, L[0]);
+                vload(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
+            } else if (limiter == 1 || limiter == 4) {
+                // min over faces of Venkatakrishnan's psi(d1, d2), capped at 1, threshold
+                // eps^2 phi_i^2 relative to the cell value (readings).  psi < 1 needs
+                // y = d2/d1 > 1/2, where psi decreases in y; so the minimum over the faces
+                // with d2 > 0 is psi(Delta_max, max d2) and over d2 < 0 psi(Delta_min, min d2):
+                // two evaluations instead of one per face (the same value up to rounding)
+                T d2hi[2][NV], d2lo[2][NV];
+#pragma unroll
+                for (int e = 0; e < NV; ++e) d2hi[0][e] = d2hi[1][e] = d2lo[0][e] = d2lo[1][e] = T(0);
+                for_faces([&](int q) {
+                    const Q4<T> B = s_B[w][q];
+#pragma unroll
+                    for (int e = 0; e < NV; ++e)
+#pragma unroll
+                        for (int fd = 0; fd < 2; ++fd) {
+                            const T d2 = g[fd][0][e] * B.x + g[fd][1][e] * B.y + g[fd][2][e] * B.z;
+                            d2hi[fd][e] = d2 > d2hi[fd][e] ? d2 : d2hi[fd][e];
+                            d2lo[fd][e] = d2 < d2lo[fd][e] ? d2 : d2lo[fd][e];
+                        }
+                });
 #pragma unroll
                 for (int e = 0; e < NV; ++e)
 #pragma unroll
                     for (int fd = 0; fd < 2; ++fd) {
-                        const T d2 = g[fd][0][e] * dx + g[fd][1][e] * dy + g[fd][2][e] * dz;
-                        d2hi[fd][e] = d2 > d2hi[fd][e] ? d2 : d2hi[fd][e];
-                        d2lo[fd][e] = d2 < d2lo[fd][e] ? d2 : d2lo[fd][e];
-                    }
-            }
-#pragma unroll
-            for (int e = 0; e < NV; ++e)
-#pragma unroll
-                for (int fd = 0; fd < 2; ++fd) {
-                    const T ph0 = fd == 0 ? pg[e] : ph[e];
-                    const T ep = eps2 * ph0 * ph0;
-                    T Lv = T(1);
+                        const T ph0 = fd == 0 ? pg[e] : ph[e];
+                        const T ep = eps2 * ph0 * ph0;
+                        T Lv = T(1);
 #if RECON_BF
-                    if constexpr (sizeof(T) == 4) {
-                        // the same minimum without branches: both quotients are formed
-                        // (their denominators are positive whenever they are selected)
-                        const T a1 = dmax[fd][e], a2 = d2hi[fd][e];
-                        const T b1 = dmin[fd][e], b2 = d2lo[fd][e];
-                        const T ra = lim_div(a1 * a1 + ep + T(2) * a1 * a2, a1 * a1 + T(2) * a2 * a2 + a1 * a2 + ep);
-                        const T rb = lim_div(b1 * b1 + ep + T(2) * b1 * b2, b1 * b1 + T(2) * b2 * b2 + b1 * b2 + ep);
-                        Lv = (a2 > T(0) && ra < Lv) ? ra : Lv;
-                        Lv = (b2 < T(0) && rb < Lv) ? rb : Lv;
-                        L[fd][e] = Lv;
-                        continue;
-                    }
+                        if constexpr (sizeof(T) == 4) {
+                            // the same minimum without branches: both quotients are formed
+                            // (their denominators are positive whenever they are selected)
+                            const T a1 = dmax[fd][e], a2 = d2hi[fd][e];
+                            const T b1 = dmin[fd][e], b2 = d2lo[fd][e];
+                            const T ra = lim_div(a1 * a1 + ep + T(2) * a1 * a2, a1 * a1 + T(2) * a2 * a2 + a1 * a2 + ep);
+                            const T rb = lim_div(b1 * b1 + ep + T(2) * b1 * b2, b1 * b1 + T(2) * b2 * b2 + b1 * b2 + ep);
+                            Lv = (a2 > T(0) && ra < Lv) ? ra : Lv;
+                            Lv = (b2 < T(0) && rb < Lv) ? rb : Lv;
+                            L[fd][e] = Lv;
+                            continue;
+                        }
 #endif
-                    if (d2hi[fd][e] > T(0)) {
-                        const T d1 = dmax[fd][e], d2 = d2hi[fd][e];
-                        const T num = d1 * d1 + ep + T(2) * d1 * d2;
-                        const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
-                        if (num < den) Lv = lim_div(num, den);
+                        if (d2hi[fd][e] > T(0)) {
+                            const T d1 = dmax[fd][e], d2 = d2hi[fd][e];
+                            const T num = d1 * d1 + ep + T(2) * d1 * d2;
+                            const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
+                            if (num < den) Lv = lim_div(num, den);
+                        }
+                        if (d2lo[fd][e] < T(0)) {
+                            const T d1 = dmin[fd][e], d2 = d2lo[fd][e];
+                            const T num = d1 * d1 + ep + T(2) * d1 * d2;
+                            const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
+                            if (num < Lv * den) Lv = lim_div(num, den);
+                        }
+                        L[fd][e] = Lv;
                     }
-                    if (d2lo[fd][e] < T(0)) {
-                        const T d1 = dmin[fd][e], d2 = d2lo[fd][e];
-                        const T num = d1 * d1 + ep + T(2) * d1 * d2;
-                        const T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + ep;
-                        if (num < Lv * den) Lv = lim_div(num, den);
-                    }
-                    L[fd][e] = Lv;
+                if (limiter == 4) {
+                    vstore(c.lstore + (size_t)i * c.Kp + k0, L[0]);
+                    vstore(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
                 }
-            if (limiter == 4) {
-                vstore(c.lstore + (size_t)i * c.Kp + k0, L[0]);
-                vstore(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
             }
-        }
-        T ux[NV], uy[NV], uz[NV];
-        vload(c.uT + k0, ux);
-        vload(c.uT + c.Kp + k0, uy);
-        vload(c.uT + 2 * c.Kp + k0, uz);
-#pragma unroll 1
-        for (int q = 0; q < ns; ++q) {
-            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
-            const T sq = s_s[w][q], dx = s_d[w][0][q], dy = s_d[w][1][q], dz = s_d[w][2][q];
-            const bool left = s_left[w][q];
-            const size_t o = (size_t)s_face[w][q] * c.Kp + k0;
-            T vg[NV], vh[NV];
-            bool up[NV], all = true;
+            T ux[NV], uy[NV], uz[NV];
+            vload(c.uT + k0, ux);
+            vload(c.uT + c.Kp + k0, uy);
+            vload(c.uT + 2 * c.Kp + k0, uz);
+            for_faces([&](int q) {
+                const Q4<T> Cn = s_C[w][q], B = s_B[w][q];
+                const int4 I = s_I[w][q];
+                const bool left = I.z;
+                const size_t o = (size_t)I.y * c.Kp + k0;
+                T vg[NV], vh[NV];
+                bool up[NV], all = true;
 #pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                const T un = dot_rn(ux[e], uy[e], uz[e], nx, ny, nz);
-                up[e] = left ? (un > T(0)) : (un <= T(0));
-                all = all && up[e];
-                const T rx = dx - ux[e] * sq, ry = dy - uy[e] * sq, rz = dz - uz[e] * sq;
-                vg[e] = pg[e] + L[0][e] * (g[0][0][e] * rx + g[0][1][e] * ry + g[0][2][e] * rz);
-                vh[e] = ph[e] + L[1][e] * (g[1][0][e] * rx + g[1][1][e] * ry + g[1][2][e] * rz);
-            }
-            if (all) {
-                vstore(c.face + o, vg);
-                vstore(c.face + FK + o, vh);
-            } else {
+                for (int e = 0; e < NV; ++e) {
+                    const T un = dot_rn(ux[e], uy[e], uz[e], Cn.x, Cn.y, Cn.z);
+                    up[e] = left ? (un > T(0)) : (un <= T(0));
+                    all = all && up[e];
+                    const T rx = B.x - ux[e] * B.w, ry = B.y - uy[e] * B.w, rz = B.z - uz[e] * B.w;
+                    vg[e] = pg[e] + L[0][e] * (g[0][0][e] * rx + g[0][1][e] * ry + g[0][2][e] * rz);
+                    vh[e] = ph[e] + L[1][e] * (g[1][0][e] * rx + g[1][1][e] * ry + g[1][2][e] * rz);
+                }
+                if (all) {
+                    vstore(c.face + o, vg);
+                    vstore(c.face + FK + o, vh);
+                } else {
 #pragma unroll
-                for (int e = 0; e < NV; ++e)
-                    if (up[e]) { c.face[o + e] = vg[e]; c.face[FK + o + e] = vh[e]; }
-            }
+                    for (int e = 0; e < NV; ++e)
+                        if (up[e]) { c.face[o + e] = vg[e]; c.face[FK + o + e] = vh[e]; }
+                }
+            });
         }
-    }
+    };
+    body();
 }
 
 // ------------------------------------------------------------------------------------

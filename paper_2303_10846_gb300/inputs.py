@@ -686,7 +686,7 @@ def cavity_workload(n: int = 8, n_gh: int = 8, kn: float = 0.075, ma_lid: float 
 
 def sphere_workload(h_wall: float = 0.065, growth: float = 1.15, h_max: float = 0.4,
                     dvs_target: int = 3000, ma: float = 5.0, kn: float = 0.1,
-                    Z_rot: float = 3.5, T_w: float = 1.0, cfl_imp: float = 1000.0,
+                    Z_rot: float = 3.5, T_w: float = 1.0, cfl_imp: float = 50.0,
                     mesh_seed: int = 20261, dvs_seed: int = 20262,
                     box_half: float = 2.5) -> Workload:
     """Sphere of diameter 1 at Mach `ma` along +x, Kn on the diameter (Sec. 4.2
@@ -715,7 +715,7 @@ def sphere_workload(h_wall: float = 0.065, growth: float = 1.15, h_max: float = 
 def capsule_workload(h_wall: float = 0.047, growth: float = 1.12, h_max: float = 0.39,
                      dvs_target: int = 6000, ma: float = 10.0, kn: float = 0.01,
                      aoa: float = 25.0, T_w: float = 300.0 / 142.0, Z_rot: float = 3.5,
-                     cfl_imp: float = 1000.0, mesh_seed: int = 20263,
+                     cfl_imp: float = 100.0, mesh_seed: int = 20263,
                      dvs_seed: int = 20264) -> Workload:
     """Blunt capsule (spherical-cap heat shield R = 1 up to the shoulder radius 0.8,
     33-degree conical afterbody to radius 0.3, flat back) at 25 degrees angle of
@@ -741,7 +741,7 @@ def capsule_workload(h_wall: float = 0.047, growth: float = 1.12, h_max: float =
 
 def cone_scale_workload(h_wall: float = 0.065, growth: float = 1.12, h_max: float = 0.45,
                         dvs_target: int = 8000, ma: float = 8.0, kn: float = 0.005,
-                        T_w: float = 1.0, Z_rot: float = 3.5, cfl_imp: float = 1000.0,
+                        T_w: float = 1.0, Z_rot: float = 3.5, cfl_imp: float = 100.0,
                         mesh_seed: int = 20265, dvs_seed: int = 20266) -> Workload:
     """Scale case: sphere-cone (nose radius 1, 15-degree half angle, length 4, flat
     base) at zero incidence, Mach 8, Kn on the nose radius, T_w = T_inf (the case gives

@@ -194,3 +194,11 @@ def test_long_mixed_run_stays_finite(sphere):
     rc, n, res = s.iterate(300)
     assert rc == 0 and n == 300
     assert np.all(np.isfinite(res)) and np.max(res) < 1e-4
+
+
+def test_sphere_mixed_converges_to_1e_6(sphere):
+    """The bench workload reaches the residual 1e-6 in mixed precision from the initial
+    field (about 100 iterations with the implicit CFL of 50)."""
+    s = _solver(sphere, "mixed")
+    rc, n, res = s.iterate(300, tol=1e-6)
+    assert rc == 0 and np.max(res) < 1e-6 and n < 300
