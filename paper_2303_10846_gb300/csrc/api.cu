@@ -35,6 +35,7 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     // RYKOV_STAGED: which micro sweeps stage their row loads (bits 0/1/2: first,
     // middle, last sweep); the results are the same either way
     if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::atoi(v) & 7;
+    if (const char* v = std::getenv("RYKOV_PRIO")) ctx->use_prio = std::strcmp(v, "0") != 0;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
     std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
@@ -550,12 +551,17 @@ static int step_impl(rk_ctx* ctx, rk::Dev<T>& d, int step) {
 // capture one whole iteration into a CUDA graph (on a private stream)
 template <typename T>
 static int build_graph(rk_ctx* ctx, rk::Dev<T>& d) {
-    if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    // with RYKOV_PRIO=1 the main branch (macro solve) is captured on a high-priority
+    // stream and the side branch (micro flux, boundary faces) on a low-priority one, and
+    // the graph runs with these per-node priorities
+    int plo = 0, phi = 0;
+    if (ctx->use_prio) CK(cudaDeviceGetStreamPriorityRange(&plo, &phi));
+    if (!ctx->cap) CK(cudaStreamCreateWithPriority(&ctx->cap, cudaStreamNonBlocking, ctx->use_prio ? phi : 0));
     const bool pon = ctx->prof.on;
     const long long l0 = ctx->prof.launches;
     ctx->prof.on = false;
     cudaGraph_t g = nullptr;
-    if (!ctx->cap2) CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
+    if (!ctx->cap2) CK(cudaStreamCreateWithPriority(&ctx->cap2, cudaStreamNonBlocking, ctx->use_prio ? plo : 0));
     if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     if (!ctx->ev_bnd) CK(cudaEventCreateWithFlags(&ctx->ev_bnd, cudaEventDisableTiming));
@@ -589,7 +595,8 @@ static int build_graph(rk_ctx* ctx, rk::Dev<T>& d) {
         if (g) cudaGraphDestroy(g);
         return fail(ctx, RK_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    cudaError_t e3 = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaError_t e3 = cudaGraphInstantiateWithFlags(&ctx->gexec, g,
+                                                   ctx->use_prio ? cudaGraphInstantiateFlagUseNodePriority : 0);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) {
         ctx->gexec = nullptr;
