@@ -551,9 +551,9 @@ static int step_impl(rk_ctx* ctx, rk::Dev<T>& d, int step) {
 // capture one whole iteration into a CUDA graph (on a private stream)
 template <typename T>
 static int build_graph(rk_ctx* ctx, rk::Dev<T>& d) {
-    // with RYKOV_PRIO=1 the main branch (macro solve) is captured on a high-priority
+    // the main branch (macro solve, the critical path) is captured on a high-priority
     // stream and the side branch (micro flux, boundary faces) on a low-priority one, and
-    // the graph runs with these per-node priorities
+    // the graph runs with these per-node priorities (RYKOV_PRIO=0: no priorities)
     int plo = 0, phi = 0;
     if (ctx->use_prio) CK(cudaDeviceGetStreamPriorityRange(&plo, &phi));
     if (!ctx->cap) CK(cudaStreamCreateWithPriority(&ctx->cap, cudaStreamNonBlocking, ctx->use_prio ? phi : 0));
