@@ -59,10 +59,11 @@ struct EqS {
 };
 
 // xb[0] rho, [1-3] U, [4] theta, [5] theta_tr, [6] theta_rot, [7-9] q_tr, [10-12] q_rot
-// += Gb dG*/dx + Hb dR*/dx at velocity u
+// += Gb dG*/dx + Hb dR*/dx at velocity u; G, H receive G*(u), R*(u) themselves (the
+// forward values come with the same exponentials)
 __device__ __forceinline__ void eq_vjp(const EqS& s, double om0, double om1, double del, double Z,
                                        double ux, double uy, double uz, double Gb, double Hb,
-                                       double* xb) {
+                                       double* xb, double& G, double& H) {
     const double c[3] = {ux - s.U[0], uy - s.U[1], uz - s.U[2]};
     const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
     const double cqt = c[0] * s.qtr[0] + c[1] * s.qtr[1] + c[2] * s.qtr[2];
@@ -80,6 +81,8 @@ __device__ __forceinline__ void eq_vjp(const EqS& s, double om0, double om1, dou
     const double Btr = (1.0 - del) * irho * itr;
     const double Br = om1 * (1.0 - del) * irho * it;
     const double a1 = 1.0 - 1.0 / Z, a2 = 1.0 / Z;
+    G = a1 * Gtr + a2 * Grot;
+    H = a1 * (s.throt * Gtr + Btr * cqr * Mtr) + a2 * (s.th * Grot + Br * cqr * M);
     const double htb = a1 * Hb, hrb = a2 * Hb;
     const double gtb = a1 * Gb + htb * s.throt;
     const double grb = a2 * Gb + hrb * s.th;
@@ -148,8 +151,6 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a,
     const Prim p = prim_from_W(W, R);
     const double tau = relax_time(c, p.rho, p.Ttr);
     const double itau = 1.0 / tau;
-    double e[EQN];
-    make_eq<double, double>(c, p.rho, p.U, p.T, p.Ttr, p.Trot, q, q + 3, e);
     const EqS st{p.rho, {p.U[0], p.U[1], p.U[2]}, R * p.T, R * p.Ttr, R * p.Trot,
                  {q[0], q[1], q[2]}, {q[3], q[4], q[5]}};
     double vW[6], vq[6];
@@ -160,8 +161,6 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a,
     for (int j = 0; j < 17; ++j) acc[j] = 0.0;
     for (int k = lane; k < c.K; k += 32) {
         const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
-        double G, H;
-        eval_eq(e, ux, uy, uz, G, H);
         const size_t o = (size_t)i * c.Kp + k;
         const double g = c.phi[o], h = c.phi[NK + o];
         const double vg = a.vphi[o], vh = a.vphi[NK + o];
@@ -178,13 +177,14 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a,
             a.ophi[NK + o] = -vh * itau + mh;
         }
         if (mode & 2) {
+            double G, H;
+            eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, vg * itau - mg, vh * itau - mh, acc, G, H);
             acc[13] -= (vg * (G - g) + vh * (H - h)) * itau * itau;
             const double dg = g - G, dh = h - H;
             const double t1 = -0.5 * w * dg, t2 = -w * dh;
             acc[14] += t1 * (vq[0] * c2 + 2.0 * cx * cvt) + t2 * vq[3];
             acc[15] += t1 * (vq[1] * c2 + 2.0 * cy * cvt) + t2 * vq[4];
             acc[16] += t1 * (vq[2] * c2 + 2.0 * cz * cvt) + t2 * vq[5];
-            eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, vg * itau - mg, vh * itau - mh, acc);
         }
     }
     if (!(mode & 2)) return;
@@ -349,8 +349,6 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
         qtr[d] = tau * 0.5 * m12[d] / dtr;
         qrot[d] = tau * m12[3 + d] / drot;
     }
-    double e[EQN];
-    make_eq<double, double>(c, rho, U, T, Ttr, Trot, qtr, qrot, e);
     const EqS st{rho, {U[0], U[1], U[2]}, Rg * T, Rg * Ttr, Rg * Trot,
                  {qtr[0], qtr[1], qtr[2]}, {qrot[0], qrot[1], qrot[2]}};
     const double ab = tau / (tau + s), bb = s / (tau + s), db = s / ((tau + s) * (tau + s));
@@ -367,9 +365,8 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
         const double wgb = wn * (vgl[k] * iVl - vgr[k] * iVr);
         const double whb = wn * (vgl[NK + k] * iVl - vgr[NK + k] * iVr);
         double G, H;
-        eval_eq(e, ux, uy, uz, G, H);
+        eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, bb * wgb, bb * whb, acc, G, H);
         acc[13] += (wgb * (g0[k] - G) + whb * (h0[k] - H)) * db;
-        eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, bb * wgb, bb * whb, acc);
     }
     warp_sum<14>(acc);
     // reverse of the interface state
