@@ -1557,8 +1557,8 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
     // faces whose loads are issued together
     constexpr int PF = LAST ? MICRO_LAST_PF : MICRO_PF;
     __shared__ T s_e[WPB][EQN + 2];
-    __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_ok[WPB][MAXF];
-    __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
+    __shared__ Q4<T> s_NA[WPB][MAXF];             // signed outward normal, A/V
+    __shared__ int2 s_NO[WPB][MAXF];              // neighbour, neighbour term used
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int t = blockIdx.x * WPB + w;
     if (t >= ncells) return;                      // whole warp: no block barriers below
@@ -1567,14 +1567,10 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
     if (lane < EQN + 2) s_e[w][lane] = (T)c.ceq[(size_t)i * CEQ + lane];
     if (lane < ns) {
         const int m = s0 + lane;
-        s_face[w][lane] = c.slot_face[m];
-        s_nbr[w][lane] = c.slot_nbr[m];
-        s_ok[w][lane] = (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour);
         const T sg = c.slot_left[m] ? T(1) : T(-1);
-        s_n[w][0][lane] = sg * c.slot_nT[m];
-        s_n[w][1][lane] = sg * c.slot_nT[c.nnz + m];
-        s_n[w][2][lane] = sg * c.slot_nT[2 * c.nnz + m];
-        s_AV[w][lane] = c.slot_AVT[m];
+        s_NA[w][lane] = Q4<T>{sg * c.slot_nT[m], sg * c.slot_nT[c.nnz + m], sg * c.slot_nT[2 * c.nnz + m],
+                              c.slot_AVT[m]};
+        s_NO[w][lane] = make_int2(c.slot_nbr[m], (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour));
     }
     __syncwarp();
     const T* e = s_e[w];
@@ -1595,23 +1591,25 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
         // over the faces is unchanged)
 #pragma unroll 1
         for (int qb = 0; qb < ns; qb += PF) {
-            T un[PF][NV], dg[PF][NV], dh[PF][NV];
+            T un[PF][NV], dg[PF][NV], dh[PF][NV], AVq[PF];
             bool okq[PF];
 #pragma unroll
             for (int qq = 0; qq < PF; ++qq) {
                 const int q = qb + qq;
                 okq[qq] = false;
                 if (q < ns) {
-                    const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+                    const Q4<T> NA = s_NA[w][q];
+                    const int2 NO = s_NO[w][q];
+                    AVq[qq] = NA.w;
                     bool neg = false;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        un[qq][v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
+                        un[qq][v] = dot_split(ux[v], uy[v], uz[v], NA.x, NA.y, NA.z);
                         neg = neg || !(un[qq][v] > T(0));
                     }
-                    okq[qq] = s_ok[w][q] && neg;
+                    okq[qq] = NO.y && neg;
                     if (okq[qq]) {
-                        const size_t oj = (size_t)s_nbr[w][q] * c.Kp + k0;
+                        const size_t oj = (size_t)NO.x * c.Kp + k0;
                         vload(c.dphi + oj, dg[qq]);
                         vload(c.dphi + NK + oj, dh[qq]);
                     }
@@ -1621,7 +1619,7 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 2 : (LAST ? MICRO_L
             for (int qq = 0; qq < PF; ++qq) {
                 const int q = qb + qq;
                 if (q >= ns) break;
-                const T AV = s_AV[w][q];
+                const T AV = AVq[qq];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (un[qq][v] > T(0)) {
