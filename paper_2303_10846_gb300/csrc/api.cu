@@ -379,8 +379,11 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
             for (int m = ctx->slot_off[i]; m < ctx->slot_off[i + 1]; ++m, ++mp) {
                 pnbr[mp] = ctx->slot_nbr[m];
                 pncol[mp] = ctx->slot_ncol[m];
+                // outward normal scaled by A_f / (2 V_i): the macro point update's flux
+                // coefficient folded into the normal
                 const double sg = ctx->slot_left[m] ? 1.0 : -1.0;
-                for (int r = 0; r < 3; ++r) pn[(size_t)r * nnz + mp] = sg * ctx->slot_n[(size_t)r * nnz + m];
+                const double c1 = 0.5 * ctx->fa[ctx->slot_face[m]] / ctx->cv[i];
+                for (int r = 0; r < 3; ++r) pn[(size_t)r * nnz + mp] = sg * c1 * ctx->slot_n[(size_t)r * nnz + m];
             }
         }
         pos_off[N] = mp;

@@ -1276,6 +1276,7 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int c
     for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += MACRO_LANES) {
         const int j = c.pslot_nbr[m];
         if (j < 0 || (first_forward && c.pslot_ncol[m] > colour)) continue;
+        // (A/2V) n: the flux coefficient is folded into the slot's normal
         const double nx = c.pslot_n[m], ny = c.pslot_n[c.nnz + m], nz = c.pslot_n[2 * c.nnz + m];
         // the iterate of neighbours is read through L2: in the cooperative solve it was
         // written by other blocks during this kernel
@@ -1284,13 +1285,18 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int c
         for (int q = 0; q < 8; ++q) P[q] = __ldcg(c.mPc + 8 * (size_t)j + q);
 #pragma unroll
         for (int q = 0; q < 6; ++q) dWj[q] = __ldcg(c.dW + 6 * (size_t)j + q);
+        // (A/2V) G_ij(W_j + dW_j): the Euler flux of the neighbour's current iterate
         const double Un = P[1] * nx + P[2] * ny + P[3] * nz;
         const double rU = P[0] * Un;
-        const double G1[6] = {rU, rU * P[1] + P[5] * nx, rU * P[2] + P[5] * ny, rU * P[3] + P[5] * nz,
-                              P[4] * Un, P[6] * Un};
-        const double c1 = c.sC[2 * (size_t)m], c2 = c.sC[2 * (size_t)m + 1];
+        o[0] += rU;
+        o[1] += rU * P[1] + P[5] * nx;
+        o[2] += rU * P[2] + P[5] * ny;
+        o[3] += rU * P[3] + P[5] * nz;
+        o[4] += P[4] * Un;
+        o[5] += P[6] * Un;
+        const double c2 = c.sC[2 * (size_t)m + 1];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) o[q] += c1 * G1[q] - c2 * dWj[q];
+        for (int q = 0; q < 6; ++q) o[q] -= c2 * dWj[q];
     }
     if (MACRO_LANES > 1) {
         const unsigned mask = MACRO_LANES == 32 ? 0xffffffffu
@@ -1689,8 +1695,8 @@ __global__ void __launch_bounds__(WPB * 32)
     constexpr int BY = NV * (int)sizeof(T);
     extern __shared__ __align__(16) unsigned char st_raw[];
     __shared__ T s_e[WPB][EQN + 2];
-    __shared__ int s_nbr[WPB][MAXF], s_ok[WPB][MAXF];
-    __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
+    __shared__ Q4<T> s_NA[WPB][MAXF];             // signed outward normal, A/V
+    __shared__ int2 s_NO[WPB][MAXF];              // neighbour, neighbour term used
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int t = blockIdx.x * WPB + w;
     if (t >= ncells) return;                      // whole warp: no block barriers below
@@ -1699,13 +1705,10 @@ __global__ void __launch_bounds__(WPB * 32)
     if (lane < EQN + 2) s_e[w][lane] = (T)c.ceq[(size_t)i * CEQ + lane];
     if (lane < ns) {
         const int m = s0 + lane;
-        s_nbr[w][lane] = c.slot_nbr[m];
-        s_ok[w][lane] = (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour);
         const T sg = c.slot_left[m] ? T(1) : T(-1);
-        s_n[w][0][lane] = sg * c.slot_nT[m];
-        s_n[w][1][lane] = sg * c.slot_nT[c.nnz + m];
-        s_n[w][2][lane] = sg * c.slot_nT[2 * c.nnz + m];
-        s_AV[w][lane] = c.slot_AVT[m];
+        s_NA[w][lane] = Q4<T>{sg * c.slot_nT[m], sg * c.slot_nT[c.nnz + m], sg * c.slot_nT[2 * c.nnz + m],
+                              c.slot_AVT[m]};
+        s_NO[w][lane] = make_int2(c.slot_nbr[m], (c.slot_nbr[m] >= 0) && !(first_forward && c.slot_ncol[m] > colour));
     }
     __syncwarp();
     const T* e = s_e[w];
@@ -1728,13 +1731,14 @@ __global__ void __launch_bounds__(WPB * 32)
             vload(c.uT + 2 * c.Kp + k0, uz);
 #pragma unroll 1
             for (int q = 0; q < ns; ++q) {
-                if (!s_ok[w][q]) continue;
-                const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+                const int2 NO = s_NO[w][q];
+                if (!NO.y) continue;
+                const Q4<T> NA = s_NA[w][q];
                 bool neg = false;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) neg = neg || !(dot_split(ux[v], uy[v], uz[v], nx, ny, nz) > T(0));
+                for (int v = 0; v < NV; ++v) neg = neg || !(dot_split(ux[v], uy[v], uz[v], NA.x, NA.y, NA.z) > T(0));
                 if (neg) {
-                    const size_t oj = (size_t)s_nbr[w][q] * c.Kp + k0;
+                    const size_t oj = (size_t)NO.x * c.Kp + k0;
                     cp_async<BY>(slot(st, 2 * q), c.dphi + oj);
                     cp_async<BY>(slot(st, 2 * q + 1), c.dphi + NK + oj);
                     mk |= 1u << q;
@@ -1769,16 +1773,16 @@ __global__ void __launch_bounds__(WPB * 32)
         for (int q = 0; q < NV; ++q) { D[q] = base; og[q] = oh[q] = T(0); }
 #pragma unroll 1
         for (int q = 0; q < ns; ++q) {
-            const T nx = s_n[w][0][q], ny = s_n[w][1][q], nz = s_n[w][2][q];
+            const Q4<T> NA = s_NA[w][q];
             T un[NV], dg[NV], dh[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) un[v] = dot_split(ux[v], uy[v], uz[v], nx, ny, nz);
+            for (int v = 0; v < NV; ++v) un[v] = dot_split(ux[v], uy[v], uz[v], NA.x, NA.y, NA.z);
             const bool okq = (m_cur >> q) & 1u;
             if (okq) {
                 vload(slot(st, 2 * q), dg);
                 vload(slot(st, 2 * q + 1), dh);
             }
-            const T AV = s_AV[w][q];
+            const T AV = NA.w;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if (un[v] > T(0)) {
