@@ -590,7 +590,9 @@ def refined_ball_cells(T: float) -> float:
 
 
 def unstructured_dvs(U_inf, T_inf: float, T_w: float, Ma: float, transitional: bool,
-                     target: int = 3000, seed: int = 20262, gamma: float = 1.4) -> DVS:
+                     target: int = 3000, seed: int = 20262, gamma: float = 1.4,
+                     radius_factor: float | None = None, centre_factor: float = 0.4,
+                     ball_radius_factor: float = 3.0, refine: bool = True) -> DVS:
     """Unstructured DVS following the generation criterion of Sec. 4.4.
 
     Outer ball: centre 0.4 U_inf, radius 3 sqrt(R T0) (transitional) or
@@ -599,14 +601,21 @@ def unstructured_dvs(U_inf, T_inf: float, T_w: float, Ma: float, transitional: b
     3 sqrt(R T_w), each with about refined_ball_cells(T) cells.  The remaining
     cells (target minus the refined ones) fill the outer ball.  Velocity points are
     tetrahedron centroids of a seeded Delaunay triangulation, weights their volumes.
+
+    For studies of the criterion: radius_factor replaces the 3 / 5 of the outer
+    radius, centre_factor the 0.4 of its centre, ball_radius_factor the 3 of the
+    refined balls; refine=False leaves the refined balls out.
     """
     from scipy.spatial import Delaunay
     U_inf = np.asarray(U_inf, dtype=np.float64)
     T0 = T_inf * (1.0 + 0.5 * (gamma - 1.0) * Ma * Ma)
-    c_out = 0.4 * U_inf
-    r_out = (3.0 if transitional else 5.0) * math.sqrt(R_GAS * T0)
-    balls = [(U_inf, 3.0 * math.sqrt(R_GAS * T_inf), refined_ball_cells(T_inf)),
-             (np.zeros(3), 3.0 * math.sqrt(R_GAS * T_w), refined_ball_cells(T_w))]
+    c_out = centre_factor * U_inf
+    rf = radius_factor if radius_factor is not None else (3.0 if transitional else 5.0)
+    r_out = rf * math.sqrt(R_GAS * T0)
+    balls = [(U_inf, ball_radius_factor * math.sqrt(R_GAS * T_inf), refined_ball_cells(T_inf)),
+             (np.zeros(3), ball_radius_factor * math.sqrt(R_GAS * T_w), refined_ball_cells(T_w))]
+    if not refine:
+        balls = []
     n_ref = sum(b[2] for b in balls)
     n_out = max(200.0, target - n_ref)
     v_ref = sum(4.0 / 3.0 * math.pi * b[1] ** 3 for b in balls)
@@ -688,7 +697,7 @@ def sphere_workload(h_wall: float = 0.065, growth: float = 1.15, h_max: float = 
                     dvs_target: int = 3000, ma: float = 5.0, kn: float = 0.1,
                     Z_rot: float = 3.5, T_w: float = 1.0, cfl_imp: float = 50.0,
                     mesh_seed: int = 20261, dvs_seed: int = 20262,
-                    box_half: float = 2.5) -> Workload:
+                    box_half: float = 2.5, dvs_options: dict | None = None) -> Workload:
     """Sphere of diameter 1 at Mach `ma` along +x, Kn on the diameter (Sec. 4.2
     shape): seeded Delaunay tetrahedra in a 10R box, unstructured DVS from the
     Sec. 4.4 criterion, farfield on the box, diffuse wall at T_w."""
@@ -696,7 +705,7 @@ def sphere_workload(h_wall: float = 0.065, growth: float = 1.15, h_max: float = 
     a = math.sqrt(1.4 * R_GAS)
     U = (ma * a, 0.0, 0.0)
     dvs = unstructured_dvs(U, 1.0, T_w, ma, transitional=(kn >= 0.1), target=dvs_target,
-                           seed=dvs_seed)
+                           seed=dvs_seed, **(dvs_options or {}))
     params = Params(Z_rot=Z_rot, mu_ref=mu_ref_from_kn(kn, 0.74), cfl_imp=cfl_imp,
                     cfl_imp0=2.0, cfl_ramp=1.3, first_order_iters=10)
     bcs = [BC(BC_WALL, 1.0, (0.0, 0.0, 0.0), T_w), BC(BC_FARFIELD, 1.0, U, 1.0)]
@@ -716,7 +725,7 @@ def capsule_workload(h_wall: float = 0.047, growth: float = 1.12, h_max: float =
                      dvs_target: int = 6000, ma: float = 10.0, kn: float = 0.01,
                      aoa: float = 25.0, T_w: float = 300.0 / 142.0, Z_rot: float = 3.5,
                      cfl_imp: float = 100.0, mesh_seed: int = 20263,
-                     dvs_seed: int = 20264) -> Workload:
+                     dvs_seed: int = 20264, dvs_options: dict | None = None) -> Workload:
     """Blunt capsule (spherical-cap heat shield R = 1 up to the shoulder radius 0.8,
     33-degree conical afterbody to radius 0.3, flat back) at 25 degrees angle of
     attack, Mach 10 along +x, Kn on the maximum diameter (1.6), T_w = 300/142 T_inf,
@@ -728,7 +737,7 @@ def capsule_workload(h_wall: float = 0.047, growth: float = 1.12, h_max: float =
     a = math.sqrt(1.4 * R_GAS)
     U = (ma * a, 0.0, 0.0)
     dvs = unstructured_dvs(U, 1.0, T_w, ma, transitional=(kn >= 0.1), target=dvs_target,
-                           seed=dvs_seed)
+                           seed=dvs_seed, **(dvs_options or {}))
     params = Params(Z_rot=Z_rot, mu_ref=mu_ref_from_kn(kn, 0.74, length=D), cfl_imp=cfl_imp,
                     cfl_imp0=2.0, cfl_ramp=1.3, first_order_iters=10)
     bcs = [BC(BC_WALL, 1.0, (0.0, 0.0, 0.0), T_w), BC(BC_FARFIELD, 1.0, U, 1.0)]

@@ -122,3 +122,40 @@ def test_capsule_and_scale_workload_sizes():
     a = math.sqrt(1.4 * I.R_GAS)
     d = I.unstructured_dvs((8 * a, 0, 0), 1.0, 1.0, 8.0, transitional=False, target=8000, seed=20266)
     assert 7_500 < d.K < 8_500
+
+
+def test_unstructured_dvs_criterion_variants():
+    """The constants of the Sec. 4.4 criterion as parameters: the defaults are the
+    criterion's (3 sqrt(R T0) transitional, centre 0.4 U), the outer radius and centre
+    follow their factors, and without refined balls the size is the target and the
+    weights fill the outer ball."""
+    U, Ma = (3.0, 0.0, 0.0), 3.0
+    T0 = 1.0 * (1.0 + 0.2 * Ma * Ma)
+    a = I.unstructured_dvs(U, 1.0, 1.0, Ma, True, target=600)
+    b = I.unstructured_dvs(U, 1.0, 1.0, Ma, True, target=600, radius_factor=3.0, centre_factor=0.4,
+                           ball_radius_factor=3.0, refine=True)
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.w, b.w)
+    for rf, cf in ((3.0, 0.4), (4.0, 0.2)):
+        d = I.unstructured_dvs(U, 1.0, 1.0, Ma, True, target=600, radius_factor=rf, centre_factor=cf,
+                               refine=False)
+        r = rf * math.sqrt(I.R_GAS * T0)
+        c = cf * np.asarray(U)
+        dist = np.linalg.norm(d.u - c, axis=1)
+        assert dist.max() <= r and dist.max() > 0.85 * r
+        assert abs(d.K - 600) < 0.25 * 600
+        vol = 4.0 / 3.0 * math.pi * r ** 3
+        assert 0.85 * vol < d.w.sum() <= vol
+        centroid = (d.w[:, None] * d.u).sum(0) / d.w.sum()
+        assert np.linalg.norm(centroid - c) < 0.05 * r
+
+
+def test_freestream_turned_by_the_angle_of_attack():
+    from paper_2303_10846_gb300 import studies as S
+    U = (2.0, 0.0, 0.0)
+    for plane in ("xz", "xy"):
+        for a in (0.0, 10.0, -25.0):
+            Ua, el = S.freestream_at(U, a, plane)
+            Ua, el = np.asarray(Ua), np.asarray(el)
+            assert abs(np.linalg.norm(Ua) - 2.0) < 1e-14 and abs(np.linalg.norm(el) - 1.0) < 1e-14
+            assert abs(Ua @ el) < 1e-14
+            assert abs(math.degrees(math.atan2(Ua[2] if plane == "xz" else Ua[1], Ua[0])) - a) < 1e-12
