@@ -855,8 +855,11 @@ __global__ void __launch_bounds__(WPB * 32, RECON_MINB) k_recon(Dev<T> c) {
 //           flux_solve_phi) and the DVS quadrature of the macro flux (Eq.
 //           implicit_mac_equ_mac_flux)
 // ------------------------------------------------------------------------------------
+#ifndef FACE_MINB
+#define FACE_MINB 1
+#endif
 template <typename T, int WPB>
-__global__ void __launch_bounds__(WPB * 32) k_face_interior(Dev<T> c) {
+__global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c) {
     using R = Red<T>;
     using V = typename R::V;
     constexpr int NV = VW<T>::N;

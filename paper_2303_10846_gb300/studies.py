@@ -2,9 +2,9 @@
 iteration and every load integral runs in the CUDA kernels of librykov).
 
 * Angle-of-attack sweeps: the lift, drag, lift-to-drag and pitching-moment curves that
-  Sec. 4 reports for the blunted cone and the capsule.  The freestream of the farfield
-  boundaries is turned in a plane; each angle continues from the previous converged
-  state.
+  Sec. 4 reports for the blunted cone and the capsule.  The freestream is turned in a
+  plane together with the velocity space built around it; each angle is converged
+  from the initial field.
 * DVS-criterion studies: the unstructured velocity-space criterion of Sec. 4.4 with
   its constants varied (outer radius factor, centre factor, refined-ball radius, with
   or without refined balls, size K), each variant iterated to convergence, so that the
@@ -18,7 +18,7 @@ import time
 import numpy as np
 
 from . import inputs as I
-from .rykov import RK_FARFIELD, RK_OK, Solver, _c, _ptr
+from .rykov import RK_FARFIELD, RK_OK, Solver
 
 
 def freestream_at(U, aoa_deg: float, plane: str = "xz"):
@@ -33,15 +33,6 @@ def freestream_at(U, aoa_deg: float, plane: str = "xz"):
     raise ValueError("plane must be 'xz' or 'xy'")
 
 
-def set_farfield_velocity(solver: Solver, U) -> None:
-    """Give every farfield boundary of the solver's workload the velocity U (density
-    and temperature unchanged)."""
-    Uc = _c(U, np.float64)
-    for b, bc in enumerate(solver.wl.bcs):
-        if bc.kind == RK_FARFIELD:
-            solver._check(solver.L.rk_set_bc(solver.h, b, RK_FARFIELD, float(bc.rho), _ptr(Uc), float(bc.T)))
-
-
 def _turn(v, aoa_deg: float, plane: str):
     """Velocity vectors v [n, 3] turned by aoa_deg in the plane of freestream_at."""
     a = math.radians(aoa_deg)
@@ -53,45 +44,49 @@ def _turn(v, aoa_deg: float, plane: str):
     return out
 
 
+def turned_workload(wl: I.Workload, aoa_deg: float, plane: str = "xz") -> I.Workload:
+    """The workload with its freestream turned by aoa_deg: farfield velocities, the
+    initial velocities and the discrete velocities all turned about the same axis, so
+    that a velocity space built around the freestream by the Sec. 4.4 criterion (outer
+    ball centred at 0.4 U_inf, refined ball at U_inf) still surrounds it.  The body and
+    the mesh stay where they are."""
+    import dataclasses
+    U0 = np.asarray(wl.ref["U"], dtype=np.float64)
+    U, _ = freestream_at(U0, aoa_deg, plane)
+    bcs = [dataclasses.replace(b, U=tuple(_turn(np.asarray([b.U], float), aoa_deg, plane)[0]))
+           if b.kind == RK_FARFIELD else b for b in wl.bcs]
+    prim = np.array(wl.prim0, dtype=np.float64, copy=True)
+    prim[:, 1:4] = _turn(prim[:, 1:4], aoa_deg, plane)
+    dvs = I.DVS(u=_turn(wl.dvs.u, aoa_deg, plane), w=wl.dvs.w, name=f"{wl.dvs.name}@{aoa_deg:g}")
+    ref = dict(wl.ref)
+    ref["U"] = tuple(U)
+    return dataclasses.replace(wl, bcs=bcs, prim0=prim, dvs=dvs, ref=ref,
+                               name=f"{wl.name}_aoa{aoa_deg:g}")
+
+
 def aoa_sweep(wl: I.Workload, angles_deg, precision: str = "mixed", n_iter: int = 600,
               tol: float = 1e-6, plane: str = "xz", x_ref=(0.0, 0.0, 0.0), S_ref: float = 1.0,
-              L_ref: float = 1.0, solver: Solver | None = None, restart: bool = True):
-    """Converge the workload at each angle of attack in turn and return one record per
-    angle: iterations, final residual, force, moment, C_D, C_L, C_m and L/D (rk_aero
-    with the turned freestream and its lift direction).
-
-    The first angle starts from the workload's initial field with its velocities turned
-    by that angle.  Each later angle continues from the previous converged state; with
-    restart=True that state is set again (rk_set_state), so that the start-up of the
-    iteration (first-order iterations, implicit-CFL ramp) damps the jump of the
-    boundary condition."""
-    import torch
-    s = solver if solver is not None else Solver(wl, precision)
+              L_ref: float = 1.0):
+    """Converge the workload at each angle of attack (turned_workload, from its initial
+    field) and return one record per angle: iterations, final residual, wall time,
+    force, moment, C_D, C_L, C_m and L/D (rk_aero with the turned freestream and its
+    lift direction)."""
     U0 = np.asarray(wl.ref["U"], dtype=np.float64)
-    rho = wl.ref["rho"]
     out = []
-    for n_a, a in enumerate(angles_deg):
+    for a in angles_deg:
+        wa = turned_workload(wl, a, plane)
         U, e_l = freestream_at(U0, a, plane)
-        set_farfield_velocity(s, U)
-        if n_a == 0:
-            prim = np.array(wl.prim0, dtype=np.float64, copy=True)
-            prim[:, 1:4] = _turn(prim[:, 1:4], a, plane)
-            s.set_state_prim(prim)
-        elif restart:
-            W, q, _ = s.moments()
-            dist = s.get_distribution()
-            Wd = torch.from_numpy(W).to(dist.device)
-            qd = torch.from_numpy(q).to(dist.device)
-            s._check(s.L.rk_set_state(s.h, _ptr(Wd), _ptr(qd), _ptr(dist), 1))
+        s = Solver(wa, precision)
         t0 = time.perf_counter()
         rc, n, res = s.iterate(n_iter, tol)
         wall = time.perf_counter() - t0
         if rc != RK_OK:
             raise RuntimeError(f"aoa_sweep: iteration failed at {a} degrees ({rc})")
-        ld = s.aero(x_ref=x_ref, S_ref=S_ref, L_ref=L_ref, lift_dir=e_l, rho_inf=rho, U_inf=U)
+        ld = s.aero(x_ref=x_ref, S_ref=S_ref, L_ref=L_ref, lift_dir=e_l, rho_inf=wl.ref["rho"], U_inf=U)
         out.append(dict(aoa=float(a), iterations=n, residual=float(np.max(res)), wall_s=wall,
                         force=ld[0:3].tolist(), moment=ld[3:6].tolist(), C_D=float(ld[6]),
                         C_L=float(ld[7]), C_m=float(ld[8]), L_over_D=float(ld[9])))
+        s.close()
     return out
 
 

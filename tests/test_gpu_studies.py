@@ -1,6 +1,5 @@
 """Angle-of-attack sweeps and DVS-criterion studies through the library (GPU), checked
 against the FP64 oracle driven through the same boundary changes."""
-import ctypes as C
 import dataclasses
 import math
 
@@ -22,24 +21,18 @@ def _tet():
 
 
 def test_aoa_sweep_matches_oracle_fp64():
-    """Two angles in turn (5 and 15 degrees in the x-z plane), five iterations each,
-    the second continuing from the first's state without a restart: the GPU's loads
-    equal the oracle's driven through the same boundary changes."""
+    """Two angles (5 and 15 degrees in the x-z plane), five iterations each from the
+    turned initial field: the GPU's loads equal the oracle's on the same turned
+    workloads (freestream, initial field and velocity space turned together)."""
     wl = _tet()
     kw = dict(x_ref=(0.1, 0.0, -0.05), S_ref=0.8, L_ref=1.2)
-    recs = S.aoa_sweep(wl, (5.0, 15.0), precision="fp64", n_iter=5, tol=0.0, restart=False, **kw)
-    o = O.Oracle(wl)
+    recs = S.aoa_sweep(wl, (5.0, 15.0), precision="fp64", n_iter=5, tol=0.0, **kw)
     U0 = np.asarray(wl.ref["U"], float)
-    prim = np.array(wl.prim0, copy=True)
-    prim[:, 1:4] = S._turn(prim[:, 1:4], 5.0, "xz")
-    o.set_state_prim(prim)
     for r, a in zip(recs, (5.0, 15.0)):
+        wa = S.turned_workload(wl, a)
         U, el = S.freestream_at(U0, a)
-        Uc = np.ascontiguousarray(U, dtype=np.float64)
-        for b, bc in enumerate(wl.bcs):
-            if bc.kind == I.BC_FARFIELD:
-                O.lib().orc_set_bc(o.h, b, int(bc.kind), float(bc.rho), Uc.ctypes.data_as(C.c_void_p),
-                                   float(bc.T))
+        assert np.allclose(wa.ref["U"], U)
+        o = O.Oracle(wa)
         o.iterate(5)
         ref = o.aero(lift_dir=el, U_inf=U, **kw)
         assert r["iterations"] == 5

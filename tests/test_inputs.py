@@ -159,3 +159,25 @@ def test_freestream_turned_by_the_angle_of_attack():
             assert abs(np.linalg.norm(Ua) - 2.0) < 1e-14 and abs(np.linalg.norm(el) - 1.0) < 1e-14
             assert abs(Ua @ el) < 1e-14
             assert abs(math.degrees(math.atan2(Ua[2] if plane == "xz" else Ua[1], Ua[0])) - a) < 1e-12
+
+
+def test_turned_workload_turns_freestream_initial_field_and_velocity_space():
+    """Turning the workload by an angle turns the farfield velocity, the initial
+    velocities and every discrete velocity about the same axis, leaving the weights,
+    the body and the mesh as they are (so a velocity space built around the freestream
+    still surrounds it)."""
+    from paper_2303_10846_gb300 import studies as S
+    from tests import workloads as TW
+    wl = TW.tiny_tet()
+    wa = S.turned_workload(wl, 20.0, "xz")
+    U, _ = S.freestream_at(wl.ref["U"], 20.0, "xz")
+    far = [b for b in wa.bcs if b.kind == I.BC_FARFIELD][0]
+    assert np.allclose(far.U, U, atol=1e-14) and np.allclose(wa.ref["U"], U, atol=1e-14)
+    assert np.array_equal(wa.dvs.w, wl.dvs.w) and wa.mesh is wl.mesh
+    assert np.allclose(np.linalg.norm(wa.dvs.u, axis=1), np.linalg.norm(wl.dvs.u, axis=1))
+    # the first moment of the DVS (weighted mean velocity) turns with the freestream
+    m0 = (wl.dvs.w[:, None] * wl.dvs.u).sum(0)
+    m1 = (wa.dvs.w[:, None] * wa.dvs.u).sum(0)
+    assert np.allclose(m1, S._turn(m0[None], 20.0, "xz")[0], atol=1e-12 * np.abs(m0).max())
+    assert np.allclose(wa.prim0[:, 1:4], S._turn(wl.prim0[:, 1:4], 20.0, "xz"))
+    assert np.array_equal(wa.prim0[:, [0, 4, 5]], wl.prim0[:, [0, 4, 5]])
