@@ -680,7 +680,7 @@ struct alignas(4 * sizeof(T)) Q4 {
     T x, y, z, w;
 };
 #ifndef RECON_MINB
-#define RECON_MINB 3
+#define RECON_MINB 4         // 64 registers, four blocks of eight warps per SM
 #endif
 template <typename T, int WPB>
 __global__ void __launch_bounds__(WPB * 32, RECON_MINB) k_recon(Dev<T> c) {
@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(WPB * 32, RECON_MINB) k_recon(Dev<T> c) {
 //           implicit_mac_equ_mac_flux)
 // ------------------------------------------------------------------------------------
 #ifndef FACE_MINB
-#define FACE_MINB 1
+#define FACE_MINB 3          // 80 registers, three blocks of eight warps per SM
 #endif
 template <typename T, int WPB>
 __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c) {
