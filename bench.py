@@ -37,7 +37,7 @@ START_ITERS = 10          # start-up iterations (first order, CFL ramp), untimed
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
 # as they stand, mixed precision, full sphere workload: one ncu capture on the same mesh
 # with every 5th velocity (K = 607), scaled by 3033/607 (traffic is proportional to K)
-NCU_TRAFFIC_MIXED = {"k_recon": 4.700e9, "k_face_interior": 5.668e9, "k_micro_sweep": 1.707e9,
+NCU_TRAFFIC_MIXED = {"k_recon": 4.709e9, "k_face_interior": 5.668e9, "k_micro_sweep": 1.705e9,
                      "k_micro_flux": 4.586e9}
 
 
@@ -274,7 +274,8 @@ def run_gpu(args, rank, world, local_rank):
            "d2h_bytes_per_step": int(6 * 8 + (Wh.numel() + qh.numel()) * 8 / done2)}
     s.set_params(wl.params)
 
-    # adjoint of the steady residual (FP64 arithmetic at the context's state): one
+    # adjoint of the steady residual at the context's state (FP32 per-velocity
+    # arithmetic with compensated sums in a mixed context, FP64 in an FP64 one): one
     # vector-Jacobian product, and a fixed number of GMRES iterations of the adjoint solve
     adj = None
     if args.adj_iters > 0:
@@ -299,7 +300,9 @@ def run_gpu(args, rank, world, local_rank):
                "vjp_cell_velocity_per_s": N * K / (vjp_ms * 1e-3),
                "gmres_krylov_dim": args.adj_krylov, "gmres_iterations": it,
                "s_per_gmres_iteration": round(tk / max(it, 1), 4),
-               "relative_residual_after": rel, "arithmetic": "f64",
+               "relative_residual_after": rel,
+               "arithmetic": "f32+f64" if args.precision == "mixed" and
+               os.environ.get("RYKOV_ADJ_FP64", "0") in ("", "0") else "f64",
                "state": f"{args.precision} context after {args.steps} end-to-end iterations"}
 
     out = None
