@@ -248,7 +248,7 @@ int rk_residual_noalloc(const double* W_new, const double* W_old, int64_t n_cell
 const char* rk_noalloc_last_error(void);
 
 
-/* ---- adjoint of the steady residual operator (FP64 arithmetic) -------------------
+/* ---- adjoint of the steady residual operator -------------------------------------
  * A steady state of the implicit iteration (Sec. 3.5 with a zero micro increment and
  * a zero macro increment) is a zero of R(X; p), X = (phi, W, q):
  *   R_phi = (phi*(W, q) - phi)/tau(W) - F(phi; p)            Eq. implicit_mic_final_equ
@@ -275,8 +275,13 @@ const char* rk_noalloc_last_error(void);
  * rk_adjoint_workspace_size(ctx, krylov_dim) bytes (256-byte aligned), bound with
  * rk_bind_adjoint_workspace after rk_bind_workspace; krylov_dim (1..64) is the
  * dimension of one GMRES restart cycle.  Rebinding the main workspace unbinds it.
- * RK_MIXED contexts: everything below is evaluated in FP64 at the context's state
- * (its FP32 distributions widened to FP64); rk_put_state rounds phi to FP32.
+ * Arithmetic: FP64 for RK_FP64 contexts.  RK_MIXED contexts evaluate at their own
+ * state (FP32 distributions; rk_put_state rounds phi to FP32) with the per-velocity
+ * work of rk_vjp, rk_objective and the GMRES preconditioner in FP32 (velocity sums
+ * compensated and combined in FP64; vectors, per-cell and per-face scalars and the
+ * Krylov arithmetic in FP64); relative accuracy ~1e-6, except that the limiter's
+ * derivative is dropped where the limited differences are below 1e-30 (far tails).
+ * The environment variable RYKOV_ADJ_FP64=1 makes mixed contexts use FP64 there too.
  *
  *   rk_steady_residual(ctx, r, on_device): r = R(X; p).
  *   rk_vjp(ctx, v, out, out_params, on_device): out = (dR/dX)^T v, out_params[6] =

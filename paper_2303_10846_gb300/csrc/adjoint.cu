@@ -2,6 +2,7 @@
 // operator"): the second workspace, the steady residual, the vector-Jacobian product,
 // the objectives and the restarted GMRES solve of (dR/dX)^T lam = -dJ/dX.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -197,6 +198,15 @@ static cudaError_t adj_sync(rk_ctx* ctx, AdjState& A) {
     return cudaGetLastError();
 }
 
+// Per-velocity arithmetic of the adjoint kernels: FP64 for FP64 contexts; FP32 with
+// compensated velocity sums for mixed-precision contexts (the state and the vectors
+// stay FP64), unless RYKOV_ADJ_FP64=1 asks for FP64 arithmetic there too
+static bool adj_fp32(const rk_ctx* ctx) {
+    if (ctx->prec != RK_MIXED) return false;
+    const char* v = std::getenv("RYKOV_ADJ_FP64");
+    return !(v && std::strcmp(v, "0") != 0);
+}
+
 // ---- kernel sequences -------------------------------------------------------------
 static rk::AdjBufs adj_bufs(rk_ctx* ctx, AdjState& A, const double* v, double* o) {
     rk::AdjBufs a{};
@@ -207,6 +217,10 @@ static rk::AdjBufs adj_bufs(rk_ctx* ctx, AdjState& A, const double* v, double* o
     a.nbg = A.nbg; a.nbs = A.nbs; a.slot_mirg = A.slot_mirg; a.slot_AVn = A.slot_AVn;
     a.tau = A.tau; a.fpar = A.fpar; a.iterp = A.iterp;
     a.obj_scale = 0.0; a.objective = 0;
+    if (ctx->prec == RK_MIXED) {
+        a.uf = ctx->df.uT; a.wf = ctx->df.wT; a.phif = ctx->df.phi;
+        a.f0f = ctx->df.face;            // written by adj_prepare's FP32 reconstruction
+    }
     a.edrag[0] = 1.0; a.edrag[1] = a.edrag[2] = 0.0;
     for (int b = 0; b < MAX_BC; ++b) {
         if (ctx->bck[b] != RK_FARFIELD) continue;
@@ -231,11 +245,22 @@ static cudaError_t adj_prepare(rk_ctx* ctx, AdjState& A) {
     if (e != cudaSuccess) return e;
     if ((e = adj_sync(ctx, A)) != cudaSuccess) return e;
     rk::Dev<double> d = dview(ctx, A);
-    d.face = A.f0;
     d.iterp = A.iterp;
-    rk::k_recon<double, 8><<<rk::cdv(ctx->N, 8), 256, 0, ctx->stream>>>(d);
+    if (adj_fp32(ctx)) {
+        // FP32 arithmetic: the context's own FP32 reconstruction, written to its face
+        // array (scratch of the iteration) and widened into f0
+        rk::Dev<float> df = ctx->df;
+        df.iterp = A.iterp;
+        rk::k_recon<float, 8><<<rk::cdv(ctx->N, 8), 256, 0, ctx->stream>>>(df);
+        rk::k_adj_upcast<<<1216, 256, 0, ctx->stream>>>(df.face, A.f0, 2 * (size_t)ctx->F * ctx->Kp);
+        A.launches += 2;
+    } else {
+        d.face = A.f0;
+        rk::k_recon<double, 8><<<rk::cdv(ctx->N, 8), 256, 0, ctx->stream>>>(d);
+        A.launches++;
+    }
     rk::k_adj_tau<<<rk::cdv(ctx->N, 256), 256, 0, ctx->stream>>>(d, A.tau);
-    A.launches += 2;
+    A.launches++;
     return cudaGetLastError();
 }
 
@@ -249,10 +274,14 @@ static cudaError_t adj_apply(rk_ctx* ctx, AdjState& A, const double* v, double* 
     const rk::Dev<double> d = dview(ctx, A);
     cudaStream_t s = ctx->stream;
     const int gc = rk::cdv(ctx->N, rk::ADJ_WPB);
-    rk::k_adj_cell<rk::ADJ_WPB><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a, 3);
+    const bool f32 = adj_fp32(ctx);
+    if (f32) rk::k_adj_cell<rk::ADJ_WPB, float><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a, 3);
+    else rk::k_adj_cell<rk::ADJ_WPB, double><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a, 3);
     A.launches += 4;
     if (ctx->Fi) {
-        rk::k_adj_face_interior<rk::ADJ_WPB><<<rk::cdv(ctx->Fi, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(d, a);
+        const int gf = rk::cdv(ctx->Fi, rk::ADJ_WPB);
+        if (f32) rk::k_adj_face_interior<rk::ADJ_WPB, float><<<gf, rk::ADJ_WPB * 32, 0, s>>>(d, a);
+        else rk::k_adj_face_interior<rk::ADJ_WPB, double><<<gf, rk::ADJ_WPB * 32, 0, s>>>(d, a);
         A.launches++;
     }
     if (ctx->Fb) {
@@ -263,8 +292,10 @@ static cudaError_t adj_apply(rk_ctx* ctx, AdjState& A, const double* v, double* 
         cudaError_t e = cudaMemsetAsync(A.pout, 0, 16 * sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    rk::k_adj_gather<rk::ADJ_WPB><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a);
-    rk::k_adj_gather2<rk::ADJ_WPB><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a);
+    if (f32) rk::k_adj_gather<rk::ADJ_WPB, float><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a);
+    else rk::k_adj_gather<rk::ADJ_WPB, double><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a);
+    if (f32) rk::k_adj_gather2<rk::ADJ_WPB, float><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a);
+    else rk::k_adj_gather2<rk::ADJ_WPB, double><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a);
     return cudaGetLastError();
 }
 
@@ -283,8 +314,12 @@ static cudaError_t adj_precond(rk_ctx* ctx, AdjState& A, const double* in, doubl
                 const int col = dir == 0 ? cc : C - 1 - cc;
                 const int lo = ctx->col_off[col], n = ctx->col_off[col + 1] - lo;
                 if (n == 0) continue;
-                rk::k_adj_sweep<rk::ADJ_WPB><<<rk::cdv(n, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(
-                    d, a, ctx->sched.col_cell + lo, n, in, out);
+                if (adj_fp32(ctx))
+                    rk::k_adj_sweep<rk::ADJ_WPB, float><<<rk::cdv(n, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(
+                        d, a, ctx->sched.col_cell + lo, n, in, out);
+                else
+                    rk::k_adj_sweep<rk::ADJ_WPB, double><<<rk::cdv(n, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(
+                        d, a, ctx->sched.col_cell + lo, n, in, out);
                 A.launches++;
             }
         }

@@ -41,7 +41,28 @@ struct AdjBufs {
     double obj_scale;            // weight of the objective seed at wall faces (0: none)
     int objective;               // 0: heat to the wall, 1: drag
     double edrag[3];             // drag direction
+    // FP32 arithmetic of a mixed context: its FP32 velocity set and distributions
+    const float *uf, *wf, *phif;
+    const float* f0f;            // [2][F][Kp] the FP32 reconstruction (phi0 at the faces)
 };
+
+// per-velocity inputs in the arithmetic type S: FP32 arrays of a mixed context when S
+// is float (no conversions), the FP64 arrays otherwise
+template <typename S>
+__device__ __forceinline__ S vel(const Dev<double>& c, const AdjBufs& a, int dim, int k) {
+    if constexpr (sizeof(S) == 4) return a.uf[(size_t)dim * c.Kp + k];
+    else return c.u[(size_t)dim * c.Kp + k];
+}
+template <typename S>
+__device__ __forceinline__ S wgt(const Dev<double>& c, const AdjBufs& a, int k) {
+    if constexpr (sizeof(S) == 4) return a.wf[k];
+    else return c.w[k];
+}
+template <typename S>
+__device__ __forceinline__ S dist(const Dev<double>& c, const AdjBufs& a, size_t o) {
+    if constexpr (sizeof(S) == 4) return a.phif[o];
+    else return c.phi[o];
+}
 
 // ------------------------------------------------------------------------------------
 // reverse mode of one Rykov equilibrium point (Eqs. eqdf_G* - eqdf_Rrot)
@@ -54,85 +75,102 @@ struct AdjBufs {
 //   R^rot = theta G^rot + w1 (1 - delta)(c.q_rot) M / (rho theta)
 // (the same functions as the forward formula, with p_rot theta_tr / theta_rot = rho
 // theta_tr simplified), G* = (1-1/Z) G^tr + G^rot/Z, R* likewise.
+template <typename S>
 struct EqS {
-    double rho, U[3], th, thtr, throt, qtr[3], qrot[3];
+    S rho, U[3], th, thtr, throt, qtr[3], qrot[3];
+    // derived constants (make_eqs): 1/rho, 1/theta_tr, 1/theta, the Maxwellian
+    // prefactors rho (2 pi theta_tr)^-3/2 and rho (2 pi theta)^-3/2, 1/(15 rho)
+    S irho, itr, it, ntr, nr, i15r;
 };
+template <typename S>
+__device__ __forceinline__ EqS<S> make_eqs(S rho, const S* U, S th, S thtr, S throt, const S* qtr,
+                                           const S* qrot) {
+    EqS<S> e;
+    e.rho = rho;
+    for (int k = 0; k < 3; ++k) { e.U[k] = U[k]; e.qtr[k] = qtr[k]; e.qrot[k] = qrot[k]; }
+    e.th = th; e.thtr = thtr; e.throt = throt;
+    e.irho = S(1) / rho; e.itr = S(1) / thtr; e.it = S(1) / th;
+    const S atr = S(2.0 * PI) * thtr, ar = S(2.0 * PI) * th;
+    e.ntr = rho / (atr * sqrt(atr));
+    e.nr = rho / (ar * sqrt(ar));
+    e.i15r = S(1) / (S(15) * rho);
+    return e;
+}
 
-// xb[0] rho, [1-3] U, [4] theta, [5] theta_tr, [6] theta_rot, [7-9] q_tr, [10-12] q_rot
-// += Gb dG*/dx + Hb dR*/dx at velocity u; G, H receive G*(u), R*(u) themselves (the
-// forward values come with the same exponentials)
-__device__ __forceinline__ void eq_vjp(const EqS& s, double om0, double om1, double del, double Z,
-                                       double ux, double uy, double uz, double Gb, double Hb,
-                                       double* xb, double& G, double& H) {
-    const double c[3] = {ux - s.U[0], uy - s.U[1], uz - s.U[2]};
-    const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-    const double cqt = c[0] * s.qtr[0] + c[1] * s.qtr[1] + c[2] * s.qtr[2];
-    const double cqr = c[0] * s.qrot[0] + c[1] * s.qrot[1] + c[2] * s.qrot[2];
-    const double irho = 1.0 / s.rho, itr = 1.0 / s.thtr, it = 1.0 / s.th;
-    const double atr = 2.0 * PI * s.thtr, ar = 2.0 * PI * s.th;
-    const double Mtr = s.rho / (atr * sqrt(atr)) * exp(-0.5 * c2 * itr);
-    const double M = s.rho / (ar * sqrt(ar)) * exp(-0.5 * c2 * it);
-    const double i15r = 1.0 / (15.0 * s.rho);
-    const double Atr = (c2 * itr - 5.0) * itr * itr * i15r;
-    const double Ar = (c2 * it - 5.0) * it * it * i15r;
-    const double Ptr = 1.0 + cqt * Atr;
-    const double Pr = 1.0 + om0 * cqt * Ar;
-    const double Gtr = Mtr * Ptr, Grot = M * Pr;
-    const double Btr = (1.0 - del) * irho * itr;
-    const double Br = om1 * (1.0 - del) * irho * it;
-    const double a1 = 1.0 - 1.0 / Z, a2 = 1.0 / Z;
+// d[0] rho, [1-3] U, [4] theta, [5] theta_tr, [6] theta_rot, [7-9] q_tr, [10-12] q_rot
+// = Gb dG*/dx + Hb dR*/dx at velocity u (written, not added); G, H receive G*(u), R*(u)
+// themselves (the forward values come with the same exponentials).  S: the arithmetic
+// type (FP64, or FP32 for the adjoint of a mixed-precision context).
+template <typename S>
+__device__ __forceinline__ void eq_vjp(const EqS<S>& s, S om0, S om1, S del, S Z, S ux, S uy, S uz,
+                                       S Gb, S Hb, S (&d)[13], S& G, S& H) {
+    const S c[3] = {ux - s.U[0], uy - s.U[1], uz - s.U[2]};
+    const S c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    const S cqt = c[0] * s.qtr[0] + c[1] * s.qtr[1] + c[2] * s.qtr[2];
+    const S cqr = c[0] * s.qrot[0] + c[1] * s.qrot[1] + c[2] * s.qrot[2];
+    const S irho = s.irho, itr = s.itr, it = s.it, i15r = s.i15r;
+    const S Mtr = s.ntr * ex(S(-0.5) * c2 * itr);
+    const S M = s.nr * ex(S(-0.5) * c2 * it);
+    const S Atr = (c2 * itr - S(5)) * itr * itr * i15r;
+    const S Ar = (c2 * it - S(5)) * it * it * i15r;
+    const S Ptr = S(1) + cqt * Atr;
+    const S Pr = S(1) + om0 * cqt * Ar;
+    const S Gtr = Mtr * Ptr, Grot = M * Pr;
+    const S Btr = (S(1) - del) * irho * itr;
+    const S Br = om1 * (S(1) - del) * irho * it;
+    const S a1 = S(1) - S(1) / Z, a2 = S(1) / Z;
     G = a1 * Gtr + a2 * Grot;
     H = a1 * (s.throt * Gtr + Btr * cqr * Mtr) + a2 * (s.th * Grot + Br * cqr * M);
-    const double htb = a1 * Hb, hrb = a2 * Hb;
-    const double gtb = a1 * Gb + htb * s.throt;
-    const double grb = a2 * Gb + hrb * s.th;
-    double rb = 0.0, thb = 0.0, thtrb = 0.0, Ub[3] = {0.0, 0.0, 0.0}, qtb[3] = {0.0, 0.0, 0.0},
-           qrb[3] = {0.0, 0.0, 0.0}, Mtrb = 0.0, Mb = 0.0;
-    xb[6] += htb * Gtr;
+    const S htb = a1 * Hb, hrb = a2 * Hb;
+    const S gtb = a1 * Gb + htb * s.throt;
+    const S grb = a2 * Gb + hrb * s.th;
+    S rb = S(0), thb = S(0), thtrb = S(0), Ub[3] = {S(0), S(0), S(0)}, qtb[3] = {S(0), S(0), S(0)},
+      qrb[3] = {S(0), S(0), S(0)}, Mtrb = S(0), Mb = S(0);
+    d[6] = htb * Gtr;
     thb += hrb * Grot;
     {   // (1 - delta) (c.q_rot) M_tr / (rho theta_tr)
-        const double X = Btr * cqr * Mtr;
-        const double cqb = htb * Btr * Mtr;
+        const S X = Btr * cqr * Mtr;
+        const S cqb = htb * Btr * Mtr;
         Mtrb += htb * Btr * cqr;
         rb -= htb * X * irho;
         thtrb -= htb * X * itr;
-        for (int d = 0; d < 3; ++d) { qrb[d] += cqb * c[d]; Ub[d] -= cqb * s.qrot[d]; }
+        for (int k = 0; k < 3; ++k) { qrb[k] += cqb * c[k]; Ub[k] -= cqb * s.qrot[k]; }
     }
     {   // w1 (1 - delta) (c.q_rot) M / (rho theta)
-        const double X = Br * cqr * M;
-        const double cqb = hrb * Br * M;
+        const S X = Br * cqr * M;
+        const S cqb = hrb * Br * M;
         Mb += hrb * Br * cqr;
         rb -= hrb * X * irho;
         thb -= hrb * X * it;
-        for (int d = 0; d < 3; ++d) { qrb[d] += cqb * c[d]; Ub[d] -= cqb * s.qrot[d]; }
+        for (int k = 0; k < 3; ++k) { qrb[k] += cqb * c[k]; Ub[k] -= cqb * s.qrot[k]; }
     }
     {   // G^tr = M_tr (1 + (c.q_tr) A_tr)
         Mtrb += gtb * Ptr;
-        const double Pb = gtb * Mtr;
-        const double cqb = Pb * Atr, Ab = Pb * cqt;
-        const double c2b = Ab * itr * itr * itr * i15r;
+        const S Pb = gtb * Mtr;
+        const S cqb = Pb * Atr, Ab = Pb * cqt;
+        const S c2b = Ab * itr * itr * itr * i15r;
         rb -= Ab * Atr * irho;
-        thtrb += Ab * (10.0 - 3.0 * c2 * itr) * itr * itr * itr * i15r;
-        for (int d = 0; d < 3; ++d) { qtb[d] += cqb * c[d]; Ub[d] -= cqb * s.qtr[d] + 2.0 * c2b * c[d]; }
+        thtrb += Ab * (S(10) - S(3) * c2 * itr) * itr * itr * itr * i15r;
+        for (int k = 0; k < 3; ++k) { qtb[k] += cqb * c[k]; Ub[k] -= cqb * s.qtr[k] + S(2) * c2b * c[k]; }
     }
     {   // G^rot = M (1 + w0 (c.q_tr) A)
         Mb += grb * Pr;
-        const double Pb = grb * M;
-        const double cqb = Pb * om0 * Ar, Ab = Pb * om0 * cqt;
-        const double c2b = Ab * it * it * it * i15r;
+        const S Pb = grb * M;
+        const S cqb = Pb * om0 * Ar, Ab = Pb * om0 * cqt;
+        const S c2b = Ab * it * it * it * i15r;
         rb -= Ab * Ar * irho;
-        thb += Ab * (10.0 - 3.0 * c2 * it) * it * it * it * i15r;
-        for (int d = 0; d < 3; ++d) { qtb[d] += cqb * c[d]; Ub[d] -= cqb * s.qtr[d] + 2.0 * c2b * c[d]; }
+        thb += Ab * (S(10) - S(3) * c2 * it) * it * it * it * i15r;
+        for (int k = 0; k < 3; ++k) { qtb[k] += cqb * c[k]; Ub[k] -= cqb * s.qtr[k] + S(2) * c2b * c[k]; }
     }
     // Maxwellians rho (2 pi theta)^-3/2 exp(-|c|^2 / (2 theta))
     rb += Mtrb * Mtr * irho + Mb * M * irho;
-    thtrb += Mtrb * Mtr * (0.5 * c2 * itr * itr - 1.5 * itr);
-    thb += Mb * M * (0.5 * c2 * it * it - 1.5 * it);
-    for (int d = 0; d < 3; ++d) Ub[d] += (Mtrb * Mtr * itr + Mb * M * it) * c[d];
-    xb[0] += rb;
-    for (int d = 0; d < 3; ++d) { xb[1 + d] += Ub[d]; xb[7 + d] += qtb[d]; xb[10 + d] += qrb[d]; }
-    xb[4] += thb;
-    xb[5] += thtrb;
+    thtrb += Mtrb * Mtr * (S(0.5) * c2 * itr * itr - S(1.5) * itr);
+    thb += Mb * M * (S(0.5) * c2 * it * it - S(1.5) * it);
+    for (int k = 0; k < 3; ++k) Ub[k] += (Mtrb * Mtr * itr + Mb * M * it) * c[k];
+    d[0] = rb;
+    for (int k = 0; k < 3; ++k) { d[1 + k] = Ub[k]; d[7 + k] = qtb[k]; d[10 + k] = qrb[k]; }
+    d[4] = thb;
+    d[5] = thtrb;
 }
 
 // ------------------------------------------------------------------------------------
@@ -140,7 +178,7 @@ __device__ __forceinline__ void eq_vjp(const EqS& s, double om0, double om1, dou
 // mode bit 0: write ophi = the cell part of (dR/dphi)^T v (the face gathers add the
 // flux part later); bit 1: write oW, oq.  One warp per cell.
 // ------------------------------------------------------------------------------------
-template <int WPB>
+template <int WPB, typename S = double>
 __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a, int mode) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * WPB + (threadIdx.x >> 5);
@@ -151,49 +189,61 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a,
     const Prim p = prim_from_W(W, R);
     const double tau = relax_time(c, p.rho, p.Ttr);
     const double itau = 1.0 / tau;
-    const EqS st{p.rho, {p.U[0], p.U[1], p.U[2]}, R * p.T, R * p.Ttr, R * p.Trot,
-                 {q[0], q[1], q[2]}, {q[3], q[4], q[5]}};
+    // per-velocity arithmetic in S (FP64, or FP32 with compensated sums)
+    const S Us[3] = {(S)p.U[0], (S)p.U[1], (S)p.U[2]};
+    const S qs[6] = {(S)q[0], (S)q[1], (S)q[2], (S)q[3], (S)q[4], (S)q[5]};
+    const EqS<S> st = make_eqs<S>((S)p.rho, Us, (S)(R * p.T), (S)(R * p.Ttr), (S)(R * p.Trot), qs, qs + 3);
+    const S itS = (S)itau, om0 = (S)c.omega0, om1 = (S)c.omega1, del = (S)c.delta, ZS = (S)Z;
     double vW[6], vq[6];
-    for (int d = 0; d < 6; ++d) { vW[d] = a.vW[6 * (size_t)i + d]; vq[d] = a.vq[6 * (size_t)i + d]; }
+    S vWs[6], vqs[6];
+    for (int d = 0; d < 6; ++d) {
+        vW[d] = a.vW[6 * (size_t)i + d]; vq[d] = a.vq[6 * (size_t)i + d];
+        vWs[d] = (S)vW[d]; vqs[d] = (S)vq[d];
+    }
     const size_t NK = (size_t)c.N * c.Kp;
-    double acc[17];
-#pragma unroll
-    for (int j = 0; j < 17; ++j) acc[j] = 0.0;
+    Acc<S> acc[17];
     for (int k = lane; k < c.K; k += 32) {
-        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+        const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k), w = wgt<S>(c, a, k);
         const size_t o = (size_t)i * c.Kp + k;
-        const double g = c.phi[o], h = c.phi[NK + o];
-        const double vg = a.vphi[o], vh = a.vphi[NK + o];
-        const double cx = ux - p.U[0], cy = uy - p.U[1], cz = uz - p.U[2];
-        const double c2 = cx * cx + cy * cy + cz * cz;
-        const double cvt = cx * vq[0] + cy * vq[1] + cz * vq[2];
-        const double cvr = cx * vq[3] + cy * vq[4] + cz * vq[5];
-        const double u2h = 0.5 * (ux * ux + uy * uy + uz * uz);
+        const S g = dist<S>(c, a, o), h = dist<S>(c, a, NK + o);
+        const S vg = (S)a.vphi[o], vh = (S)a.vphi[NK + o];
+        const S cx = ux - Us[0], cy = uy - Us[1], cz = uz - Us[2];
+        const S c2 = cx * cx + cy * cy + cz * cz;
+        const S cvt = cx * vqs[0] + cy * vqs[1] + cz * vqs[2];
+        const S cvr = cx * vqs[3] + cy * vqs[4] + cz * vqs[5];
+        const S u2h = S(0.5) * (ux * ux + uy * uy + uz * uz);
         // weights of phi in the compensation rows (moments Psi and the heat fluxes)
-        const double mg = w * (vW[0] + ux * vW[1] + uy * vW[2] + uz * vW[3] + u2h * vW[4] + 0.5 * c2 * cvt);
-        const double mh = w * (vW[4] + vW[5] + cvr);
+        const S mg = w * (vWs[0] + ux * vWs[1] + uy * vWs[2] + uz * vWs[3] + u2h * vWs[4] + S(0.5) * c2 * cvt);
+        const S mh = w * (vWs[4] + vWs[5] + cvr);
         if (mode & 1) {
-            a.ophi[o] = -vg * itau + mg;
-            a.ophi[NK + o] = -vh * itau + mh;
+            a.ophi[o] = (double)(-vg * itS + mg);
+            a.ophi[NK + o] = (double)(-vh * itS + mh);
         }
         if (mode & 2) {
-            double G, H;
-            eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, vg * itau - mg, vh * itau - mh, acc, G, H);
-            acc[13] -= (vg * (G - g) + vh * (H - h)) * itau * itau;
-            const double dg = g - G, dh = h - H;
-            const double t1 = -0.5 * w * dg, t2 = -w * dh;
-            acc[14] += t1 * (vq[0] * c2 + 2.0 * cx * cvt) + t2 * vq[3];
-            acc[15] += t1 * (vq[1] * c2 + 2.0 * cy * cvt) + t2 * vq[4];
-            acc[16] += t1 * (vq[2] * c2 + 2.0 * cz * cvt) + t2 * vq[5];
+            S G, H, dd[13];
+            eq_vjp<S>(st, om0, om1, del, ZS, ux, uy, uz, vg * itS - mg, vh * itS - mh, dd, G, H);
+#pragma unroll
+            for (int j = 0; j < 13; ++j) acc[j].add(dd[j]);
+            acc[13].add(-((vg * (G - g) + vh * (H - h)) * itS * itS));
+            const S dg = g - G, dh = h - H;
+            const S t1 = S(-0.5) * w * dg, t2 = -w * dh;
+            acc[14].add(t1 * (vqs[0] * c2 + S(2) * cx * cvt) + t2 * vqs[3]);
+            acc[15].add(t1 * (vqs[1] * c2 + S(2) * cy * cvt) + t2 * vqs[4]);
+            acc[16].add(t1 * (vqs[2] * c2 + S(2) * cz * cvt) + t2 * vqs[5]);
         }
     }
     if (!(mode & 2)) return;
-    warp_sum<17>(acc);
+    typename Red<S>::V v[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) v[j] = Red<S>::from(acc[j]);
+    warp_red<S, 17>(v);
     if (lane != 0) return;
-    double rb = acc[0], Ub[3] = {acc[1] + acc[14], acc[2] + acc[15], acc[3] + acc[16]};
-    double Tb = R * acc[4], Ttrb = R * acc[5], Trotb = R * acc[6], taub = acc[13];
+    double t[17];
+    for (int j = 0; j < 17; ++j) t[j] = Red<S>::to_d(v[j]);
+    double rb = t[0], Ub[3] = {t[1] + t[14], t[2] + t[15], t[3] + t[16]};
+    double Tb = R * t[4], Ttrb = R * t[5], Trotb = R * t[6], taub = t[13];
     double qb[6];
-    for (int d = 0; d < 6; ++d) qb[d] = acc[7 + d];
+    for (int d = 0; d < 6; ++d) qb[d] = t[7 + d];
     double Wb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, -vW[5]};
     // rotational-energy row: + rho R ((1 - 1/Z) T_rot + T/Z) - rho E_rot
     rb += vW[5] * R * ((1.0 - 1.0 / Z) * p.Trot + p.T / Z);
@@ -296,7 +346,7 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_residual(Dev<double> c, AdjBuf
 //   scalar    : reverse of the interface state down to the moments
 //   pass B    : adjoint of phi0, written to fbar
 // ------------------------------------------------------------------------------------
-template <int WPB>
+template <int WPB, typename S = double>
 __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, AdjBufs a) {
     const int lane = threadIdx.x & 31;
     const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
@@ -304,19 +354,31 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
     const int f = c.face_int[fi];
     const int cl = c.fc[2 * f], cr = c.fc[2 * f + 1];
     const size_t FK = (size_t)c.F * c.Kp, NK = (size_t)c.N * c.Kp;
-    const double* g0 = a.f0 + (size_t)f * c.Kp;
-    const double* h0 = a.f0 + FK + (size_t)f * c.Kp;
+    // phi0 at this face in the arithmetic type (the FP32 reconstruction for S = float)
+    const S* g0;
+    if constexpr (sizeof(S) == 4) g0 = a.f0f + (size_t)f * c.Kp;
+    else g0 = a.f0 + (size_t)f * c.Kp;
+    const S* h0 = g0 + FK;
     const double Rg = c.R, Z = c.Z, s = c.fs[f];
-    double m6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int k = lane; k < c.K; k += 32) {
-        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
-        const double wg = w * g0[k], wh = w * h0[k];
-        m6[0] += wg;
-        m6[1] += wg * ux; m6[2] += wg * uy; m6[3] += wg * uz;
-        m6[4] += 0.5 * (ux * ux + uy * uy + uz * uz) * wg + wh;
-        m6[5] += wh;
+    using RS = Red<S>;
+    double m6[6];
+    {
+        Acc<S> am[6];
+        for (int k = lane; k < c.K; k += 32) {
+            const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k), w = wgt<S>(c, a, k);
+            const S wg = w * (S)g0[k], wh = w * (S)h0[k];
+            am[0].add(wg);
+            am[1].add(wg * ux); am[2].add(wg * uy); am[3].add(wg * uz);
+            am[4].add(S(0.5) * (ux * ux + uy * uy + uz * uz) * wg + wh);
+            am[5].add(wh);
+        }
+        typename RS::V v[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) v[j] = RS::from(am[j]);
+        warp_red<S, 6>(v);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) m6[j] = RS::to_d(v[j]);
     }
-    warp_sum<6>(m6);
     const double rho = m6[0], E = m6[4], Er0 = m6[5];
     const double U[3] = {m6[1] / rho, m6[2] / rho, m6[3] / rho};
     const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
@@ -329,19 +391,26 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
     const double Trot = Erot / (rho * Rg);
     const double Ttr = (E - ke - Erot) / (1.5 * rho * Rg);
     double m12[12];
+    {
+        const S Us[3] = {(S)U[0], (S)U[1], (S)U[2]};
+        Acc<S> am[12];
+        for (int k = lane; k < c.K; k += 32) {
+            const S cx = vel<S>(c, a, 0, k) - Us[0], cy = vel<S>(c, a, 1, k) - Us[1], cz = vel<S>(c, a, 2, k) - Us[2];
+            const S w = wgt<S>(c, a, k);
+            const S wg = w * (S)g0[k], wh = w * (S)h0[k];
+            const S wgc2 = wg * (cx * cx + cy * cy + cz * cz);
+            am[0].add(wgc2 * cx); am[1].add(wgc2 * cy); am[2].add(wgc2 * cz);
+            am[3].add(wh * cx); am[4].add(wh * cy); am[5].add(wh * cz);
+            am[6].add(wg * cx * cx); am[7].add(wg * cy * cy); am[8].add(wg * cz * cz);
+            am[9].add(wg * cx * cy); am[10].add(wg * cx * cz); am[11].add(wg * cy * cz);
+        }
+        typename RS::V v[12];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) m12[j] = 0.0;
-    for (int k = lane; k < c.K; k += 32) {
-        const double cx = c.u[k] - U[0], cy = c.u[c.Kp + k] - U[1], cz = c.u[2 * c.Kp + k] - U[2];
-        const double w = c.w[k];
-        const double wg = w * g0[k], wh = w * h0[k];
-        const double wgc2 = wg * (cx * cx + cy * cy + cz * cz);
-        m12[0] += wgc2 * cx; m12[1] += wgc2 * cy; m12[2] += wgc2 * cz;
-        m12[3] += wh * cx; m12[4] += wh * cy; m12[5] += wh * cz;
-        m12[6] += wg * cx * cx; m12[7] += wg * cy * cy; m12[8] += wg * cz * cz;
-        m12[9] += wg * cx * cy; m12[10] += wg * cx * cz; m12[11] += wg * cy * cz;
+        for (int j = 0; j < 12; ++j) v[j] = RS::from(am[j]);
+        warp_red<S, 12>(v);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) m12[j] = RS::to_d(v[j]);
     }
-    warp_sum<12>(m12);
     const double dtr = tau + s - s / 3.0 * (1.0 - 1.0 / Z + c.omega0 / Z);
     const double drot = tau + s - s * (1.0 - c.delta) * (1.0 - 1.0 / Z + c.omega1 / Z);
     double qtr[3], qrot[3];
@@ -349,26 +418,38 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
         qtr[d] = tau * 0.5 * m12[d] / dtr;
         qrot[d] = tau * m12[3 + d] / drot;
     }
-    const EqS st{rho, {U[0], U[1], U[2]}, Rg * T, Rg * Ttr, Rg * Trot,
-                 {qtr[0], qtr[1], qtr[2]}, {qrot[0], qrot[1], qrot[2]}};
+    const S Us[3] = {(S)U[0], (S)U[1], (S)U[2]};
+    const S qts[3] = {(S)qtr[0], (S)qtr[1], (S)qtr[2]}, qrs[3] = {(S)qrot[0], (S)qrot[1], (S)qrot[2]};
+    const EqS<S> st = make_eqs<S>((S)rho, Us, (S)(Rg * T), (S)(Rg * Ttr), (S)(Rg * Trot), qts, qrs);
+    const S om0 = (S)c.omega0, om1 = (S)c.omega1, del = (S)c.delta, ZS = (S)Z;
     const double ab = tau / (tau + s), bb = s / (tau + s), db = s / ((tau + s) * (tau + s));
     const double nx = c.fn[f], ny = c.fn[c.F + f], nz = c.fn[2 * c.F + f], A = c.fa[f];
     const double iVl = 1.0 / c.vol[cl], iVr = 1.0 / c.vol[cr];
     const double* vgl = a.vphi + (size_t)cl * c.Kp;
     const double* vgr = a.vphi + (size_t)cr * c.Kp;
     double acc[14];
+    {
+        const S nxs = (S)nx, nys = (S)ny, nzs = (S)nz, As = (S)A, iVls = (S)iVl, iVrs = (S)iVr;
+        const S bbs = (S)bb, dbs = (S)db;
+        Acc<S> am[14];
+        for (int k = lane; k < c.K; k += 32) {
+            const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k);
+            const S wn = -As * dot_rn(ux, uy, uz, nxs, nys, nzs);
+            const S wgb = wn * ((S)vgl[k] * iVls - (S)vgr[k] * iVrs);
+            const S whb = wn * ((S)vgl[NK + k] * iVls - (S)vgr[NK + k] * iVrs);
+            S G, H, dd[13];
+            eq_vjp<S>(st, om0, om1, del, ZS, ux, uy, uz, bbs * wgb, bbs * whb, dd, G, H);
 #pragma unroll
-    for (int j = 0; j < 14; ++j) acc[j] = 0.0;
-    for (int k = lane; k < c.K; k += 32) {
-        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k];
-        const double wn = -A * dot_rn(ux, uy, uz, nx, ny, nz);
-        const double wgb = wn * (vgl[k] * iVl - vgr[k] * iVr);
-        const double whb = wn * (vgl[NK + k] * iVl - vgr[NK + k] * iVr);
-        double G, H;
-        eq_vjp(st, c.omega0, c.omega1, c.delta, Z, ux, uy, uz, bb * wgb, bb * whb, acc, G, H);
-        acc[13] += (wgb * (g0[k] - G) + whb * (h0[k] - H)) * db;
+            for (int j = 0; j < 13; ++j) am[j].add(dd[j]);
+            am[13].add((wgb * ((S)g0[k] - G) + whb * ((S)h0[k] - H)) * dbs);
+        }
+        typename RS::V v[14];
+#pragma unroll
+        for (int j = 0; j < 14; ++j) v[j] = RS::from(am[j]);
+        warp_red<S, 14>(v);
+#pragma unroll
+        for (int j = 0; j < 14; ++j) acc[j] = RS::to_d(v[j]);
     }
-    warp_sum<14>(acc);
     // reverse of the interface state
     double rb = acc[0], Ub[3] = {acc[1], acc[2], acc[3]};
     double Tb = Rg * acc[4], Ttrb = Rg * acc[5], Trotb = Rg * acc[6], taub = acc[13];
@@ -413,17 +494,20 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
     rb -= UbU / rho;
     double* gb = a.fbar + (size_t)f * c.Kp;
     double* hb = a.fbar + FK + (size_t)f * c.Kp;
+    const S nxs = (S)nx, nys = (S)ny, nzs = (S)nz, As = (S)A, iVls = (S)iVl, iVrs = (S)iVr, abs_ = (S)ab;
+    const S rbs = (S)rb, mbs[3] = {(S)mb[0], (S)mb[1], (S)mb[2]}, Ebs = (S)Eb, Eh = (S)(Eb + Er0b);
+    const S Qts[3] = {(S)Qtb[0], (S)Qtb[1], (S)Qtb[2]}, Qrs[3] = {(S)Qrb[0], (S)Qrb[1], (S)Qrb[2]};
     for (int k = lane; k < c.K; k += 32) {
-        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
-        const double wn = -A * dot_rn(ux, uy, uz, nx, ny, nz);
-        const double wgb = wn * (vgl[k] * iVl - vgr[k] * iVr);
-        const double whb = wn * (vgl[NK + k] * iVl - vgr[NK + k] * iVr);
-        const double cx = ux - U[0], cy = uy - U[1], cz = uz - U[2];
-        const double c2 = cx * cx + cy * cy + cz * cz;
-        gb[k] = ab * wgb + w * (rb + mb[0] * ux + mb[1] * uy + mb[2] * uz +
-                                Eb * 0.5 * (ux * ux + uy * uy + uz * uz) +
-                                c2 * (Qtb[0] * cx + Qtb[1] * cy + Qtb[2] * cz));
-        hb[k] = ab * whb + w * (Eb + Er0b + Qrb[0] * cx + Qrb[1] * cy + Qrb[2] * cz);
+        const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k), w = wgt<S>(c, a, k);
+        const S wn = -As * dot_rn(ux, uy, uz, nxs, nys, nzs);
+        const S wgb = wn * ((S)vgl[k] * iVls - (S)vgr[k] * iVrs);
+        const S whb = wn * ((S)vgl[NK + k] * iVls - (S)vgr[NK + k] * iVrs);
+        const S cx = ux - Us[0], cy = uy - Us[1], cz = uz - Us[2];
+        const S c2 = cx * cx + cy * cy + cz * cz;
+        gb[k] = (double)(abs_ * wgb + w * (rbs + mbs[0] * ux + mbs[1] * uy + mbs[2] * uz +
+                                         Ebs * S(0.5) * (ux * ux + uy * uy + uz * uz) +
+                                         c2 * (Qts[0] * cx + Qts[1] * cy + Qts[2] * cz)));
+        hb[k] = (double)(abs_ * whb + w * (Eh + Qrs[0] * cx + Qrs[1] * cy + Qrs[2] * cz));
     }
 }
 
@@ -564,10 +648,10 @@ __global__ void __launch_bounds__(BS) k_adj_face_boundary(Dev<double> c, AdjBufs
 // gradient adjoint and the Delta_max/min adjoint with the slot of the neighbour that
 // gave it, for the neighbours to gather.  One warp per cell.
 // ------------------------------------------------------------------------------------
-template <int WPB>
+template <int WPB, typename S = double>
 __global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs a) {
     __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_left[WPB][MAXF];
-    __shared__ double s_lsq[WPB][3][MAXF], s_d[WPB][3][MAXF], s_n[WPB][3][MAXF], s_s[WPB][MAXF];
+    __shared__ S s_lsq[WPB][3][MAXF], s_d[WPB][3][MAXF], s_n[WPB][3][MAXF], s_s[WPB][MAXF];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int i = blockIdx.x * WPB + wp;
     if (i >= c.N) return;
@@ -578,96 +662,117 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs 
         s_face[wp][lane] = f;
         s_nbr[wp][lane] = c.slot_nbr[m];
         s_left[wp][lane] = c.slot_left[m];
-        s_s[wp][lane] = c.fs[f];
+        s_s[wp][lane] = (S)c.fs[f];
         for (int r = 0; r < 3; ++r) {
-            s_lsq[wp][r][lane] = c.slot_lsq[r * c.nnz + m];
-            s_d[wp][r][lane] = c.slot_d[r * c.nnz + m];
-            s_n[wp][r][lane] = c.slot_n[r * c.nnz + m];
+            s_lsq[wp][r][lane] = (S)c.slot_lsq[r * c.nnz + m];
+            s_d[wp][r][lane] = (S)c.slot_d[r * c.nnz + m];
+            s_n[wp][r][lane] = (S)c.slot_n[r * c.nnz + m];
         }
     }
     __syncwarp();
-    const double eps2 = c.eps2[i];
+    const S eps2 = (S)c.eps2[i];
     const int limiter = (int)a.iterp[1];
     const size_t NK = (size_t)c.N * c.Kp, FK = (size_t)c.F * c.Kp;
     for (int k = lane; k < c.K; k += 32) {
-        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k];
+        const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k);
         for (int fd = 0; fd < 2; ++fd) {
-            const double* ph = c.phi + fd * NK;
-            const double pc = ph[(size_t)i * c.Kp + k];
+            const size_t fo = fd * NK;
+            const S pc = dist<S>(c, a, fo + (size_t)i * c.Kp + k);
             // forward: gradient, Delta_max/min with the slot that gave them
-            double g[3] = {0.0, 0.0, 0.0}, dmax = 0.0, dmin = 0.0;
+            S g[3] = {S(0), S(0), S(0)}, dmax = S(0), dmin = S(0);
             int amax = -1, amin = -1;
             for (int q = 0; q < ns; ++q) {
                 const int j = s_nbr[wp][q];
                 if (j < 0) continue;
-                const double dp = ph[(size_t)j * c.Kp + k] - pc;
+                const S dp = dist<S>(c, a, fo + (size_t)j * c.Kp + k) - pc;
                 g[0] += s_lsq[wp][0][q] * dp; g[1] += s_lsq[wp][1][q] * dp; g[2] += s_lsq[wp][2][q] * dp;
                 if (dp > dmax) { dmax = dp; amax = q; }
                 if (dp < dmin) { dmin = dp; amin = q; }
             }
-            double L = (limiter == 2) ? 0.0 : 1.0;
+            S L = (limiter == 2) ? S(0) : S(1);
             int lq = -1;
             if (limiter == 3) {
-                L = c.lstore[fd * NK + (size_t)i * c.Kp + k];     // frozen: a constant
+                L = (S)c.lstore[fd * NK + (size_t)i * c.Kp + k];  // frozen: a constant
             } else if (limiter == 1) {
                 // the forward kernel's minimum: psi at the face of largest d2 (with
                 // Delta_max) and at the face of smallest d2 (with Delta_min)
-                double d2hi = 0.0, d2lo = 0.0;
+                S d2hi = S(0), d2lo = S(0);
                 int qhi = -1, qlo = -1;
                 for (int q = 0; q < ns; ++q) {
-                    const double d2 = g[0] * s_d[wp][0][q] + g[1] * s_d[wp][1][q] + g[2] * s_d[wp][2][q];
+                    const S d2 = g[0] * s_d[wp][0][q] + g[1] * s_d[wp][1][q] + g[2] * s_d[wp][2][q];
                     if (d2 > d2hi) { d2hi = d2; qhi = q; }
                     if (d2 < d2lo) { d2lo = d2; qlo = q; }
                 }
-                const double ep = eps2 * pc * pc;
+                const S ep = eps2 * pc * pc;
                 if (qhi >= 0) {
-                    const double d1 = dmax, d2 = d2hi;
-                    const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
-                    const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
-                    if (nu < de) { L = nu / de; lq = qhi; }
+                    const S d1 = dmax, d2 = d2hi;
+                    const S nu = d1 * d1 + ep + S(2) * d1 * d2;
+                    const S de = d1 * d1 + S(2) * d2 * d2 + d1 * d2 + ep;
+                    if (nu < de) { L = lim_div(nu, de); lq = qhi; }
                 }
                 if (qlo >= 0) {
-                    const double d1 = dmin, d2 = d2lo;
-                    const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
-                    const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
-                    if (nu < L * de) { L = nu / de; lq = qlo; }
+                    const S d1 = dmin, d2 = d2lo;
+                    const S nu = d1 * d1 + ep + S(2) * d1 * d2;
+                    const S de = d1 * d1 + S(2) * d2 * d2 + d1 * d2 + ep;
+                    if (nu < L * de) { L = lim_div(nu, de); lq = qlo; }
                 }
             }
             // adjoint of phi0 gathered over the faces where this cell is upwind
-            double self = 0.0, Gb[3] = {0.0, 0.0, 0.0};
+            S self = S(0), Gb[3] = {S(0), S(0), S(0)};
             const double* fb = a.fbar + fd * FK;
             for (int q = 0; q < ns; ++q) {
-                const double un = dot_rn(ux, uy, uz, s_n[wp][0][q], s_n[wp][1][q], s_n[wp][2][q]);
-                const bool up = s_left[wp][q] ? (un > 0.0) : (un <= 0.0);
+                const S un = dot_rn(ux, uy, uz, s_n[wp][0][q], s_n[wp][1][q], s_n[wp][2][q]);
+                const bool up = s_left[wp][q] ? (un > S(0)) : (un <= S(0));
                 if (!up) continue;
-                const double x = fb[(size_t)s_face[wp][q] * c.Kp + k];
-                const double sq = s_s[wp][q];
+                const S x = (S)fb[(size_t)s_face[wp][q] * c.Kp + k];
+                const S sq = s_s[wp][q];
                 self += x;
                 Gb[0] += (s_d[wp][0][q] - ux * sq) * x;
                 Gb[1] += (s_d[wp][1][q] - uy * sq) * x;
                 Gb[2] += (s_d[wp][2][q] - uz * sq) * x;
             }
             // reverse of L g
-            const double Lb = Gb[0] * g[0] + Gb[1] * g[1] + Gb[2] * g[2];
-            double gb[3] = {L * Gb[0], L * Gb[1], L * Gb[2]};
-            double d1b = 0.0;
+            const S Lb = Gb[0] * g[0] + Gb[1] * g[1] + Gb[2] * g[2];
+            S gb[3] = {L * Gb[0], L * Gb[1], L * Gb[2]};
+            S d1b = S(0);
             int slot = -1;
             if (limiter == 1 && lq >= 0) {
-                const double dx = s_d[wp][0][lq], dy = s_d[wp][1][lq], dz = s_d[wp][2][lq];
-                const double d2 = g[0] * dx + g[1] * dy + g[2] * dz;
-                const double d1 = d2 > 0.0 ? dmax : dmin;
-                const double ep = eps2 * pc * pc;
-                const double nu = d1 * d1 + ep + 2.0 * d1 * d2;
-                const double de = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + ep;
-                const double ide2 = 1.0 / (de * de);
-                const double pd1 = ((2.0 * d1 + 2.0 * d2) * de - nu * (2.0 * d1 + d2)) * ide2;
-                const double pd2 = (2.0 * d1 * de - nu * (4.0 * d2 + d1)) * ide2;
-                const double pep = (de - nu) * ide2;
-                gb[0] += Lb * pd2 * dx; gb[1] += Lb * pd2 * dy; gb[2] += Lb * pd2 * dz;
-                self += Lb * pep * 2.0 * eps2 * pc;
-                const int arg = d2 > 0.0 ? amax : amin;
+                const S dx = s_d[wp][0][lq], dy = s_d[wp][1][lq], dz = s_d[wp][2][lq];
+                const S d2 = g[0] * dx + g[1] * dy + g[2] * dz;
+                const S d1 = d2 > S(0) ? dmax : dmin;
+                const S ep = eps2 * pc * pc;
+                S Lp2, Lself, Lp1;          // Lb times the partial derivatives of psi
+                if constexpr (sizeof(S) == 8) {
+                    const S nu = d1 * d1 + ep + S(2) * d1 * d2;
+                    const S de = d1 * d1 + S(2) * d2 * d2 + d1 * d2 + ep;
+                    const S ide2 = S(1) / (de * de);
+                    Lp1 = Lb * (((S(2) * d1 + S(2) * d2) * de - nu * (S(2) * d1 + d2)) * ide2);
+                    Lp2 = Lb * ((S(2) * d1 * de - nu * (S(4) * d2 + d1)) * ide2);
+                    Lself = Lb * ((de - nu) * ide2) * S(2) * eps2 * pc;    // through ep
+                } else {
+                    // FP32: psi is homogeneous of degree 0 in (d1, d2, sqrt(ep)); its
+                    // derivatives are formed from the values scaled by
+                    // sigma = max(|d1|, |d2|) and divided by sigma (sigma^2 for ep), which
+                    // keeps them in range.  Below sigma = 1e-30 (the far tails of the
+                    // distributions) the limiter is taken as constant.
+                    const S sg = fmaxf(fabsf(d1), fabsf(d2));
+                    Lp1 = Lp2 = Lself = S(0);
+                    if (sg > S(1e-30)) {
+                        const S is = S(1) / sg, a1 = d1 * is, a2 = d2 * is, e = (ep * is) * is;
+                        const S nu = a1 * a1 + e + S(2) * a1 * a2;
+                        const S de = a1 * a1 + S(2) * a2 * a2 + a1 * a2 + e;
+                        const S ide2 = S(1) / (de * de);
+                        const S Lbs = Lb * is;
+                        Lp1 = Lbs * (((S(2) * a1 + S(2) * a2) * de - nu * (S(2) * a1 + a2)) * ide2);
+                        Lp2 = Lbs * ((S(2) * a1 * de - nu * (S(4) * a2 + a1)) * ide2);
+                        Lself = (Lbs * ((de - nu) * ide2)) * ((S(2) * eps2 * pc) * is);
+                    }
+                }
+                gb[0] += Lp2 * dx; gb[1] += Lp2 * dy; gb[2] += Lp2 * dz;
+                self += Lself;
+                const int arg = d2 > S(0) ? amax : amin;
                 if (arg >= 0) {
-                    d1b = Lb * pd1;
+                    d1b = Lp1;
                     self -= d1b;
                     slot = arg;
                 }
@@ -678,8 +783,9 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs 
                 self -= s_lsq[wp][0][q] * gb[0] + s_lsq[wp][1][q] * gb[1] + s_lsq[wp][2][q] * gb[2];
             }
             const size_t o = (size_t)i * c.Kp + k;
-            a.ophi[fd * NK + o] += self;
-            double* nb = a.nbg + (size_t)fd * 4 * NK;
+            a.ophi[fd * NK + o] += (double)self;
+            // the gradient and Delta adjoints, stored in the arithmetic type
+            S* nb = reinterpret_cast<S*>(a.nbg) + (size_t)fd * 4 * NK;
             nb[o] = gb[0];
             nb[NK + o] = gb[1];
             nb[2 * NK + o] = gb[2];
@@ -692,7 +798,7 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs 
 // cell gather 2: the neighbours' gradient and Delta terms that involve this cell's
 // value: sum over neighbours c of  lsq_c(this) . gb_c  +  [c's Delta came from this
 // cell] d1b_c.  One warp per cell.
-template <int WPB>
+template <int WPB, typename S = double>
 __global__ void __launch_bounds__(WPB * 32) k_adj_gather2(Dev<double> c, AdjBufs a) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * WPB + (threadIdx.x >> 5);
@@ -700,24 +806,24 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_gather2(Dev<double> c, AdjBufs
     const int s0 = c.slot_off[i], s1 = c.slot_off[i + 1];
     const size_t NK = (size_t)c.N * c.Kp;
     for (int k = lane; k < c.K; k += 32) {
-        double acc[2] = {0.0, 0.0};
+        S acc[2] = {S(0), S(0)};
         for (int m = s0; m < s1; ++m) {
             const int j = c.slot_nbr[m];
             if (j < 0) continue;
             const int mm = a.slot_mirg[m];
             const int loc = mm - c.slot_off[j];
-            const double lx = c.slot_lsq[mm], ly = c.slot_lsq[c.nnz + mm], lz = c.slot_lsq[2 * c.nnz + mm];
+            const S lx = (S)c.slot_lsq[mm], ly = (S)c.slot_lsq[c.nnz + mm], lz = (S)c.slot_lsq[2 * c.nnz + mm];
             const size_t o = (size_t)j * c.Kp + k;
             for (int fd = 0; fd < 2; ++fd) {
-                const double* nb = a.nbg + (size_t)fd * 4 * NK;
-                double t = lx * nb[o] + ly * nb[NK + o] + lz * nb[2 * NK + o];
+                const S* nb = reinterpret_cast<const S*>(a.nbg) + (size_t)fd * 4 * NK;
+                S t = lx * nb[o] + ly * nb[NK + o] + lz * nb[2 * NK + o];
                 if (a.nbs[fd * NK + o] == loc) t += nb[3 * NK + o];
                 acc[fd] += t;
             }
         }
         const size_t o = (size_t)i * c.Kp + k;
-        a.ophi[o] += acc[0];
-        a.ophi[NK + o] += acc[1];
+        a.ophi[o] += (double)acc[0];
+        a.ophi[NK + o] += (double)acc[1];
     }
 }
 
@@ -739,7 +845,7 @@ __global__ void k_adj_params(const double* fpar, int Fb, double* out) {
 // (the transpose of the micro PR-SGS operator: entry (i, j) is (A/V_j) min(u.n_ji, 0)).
 // One warp per cell.
 // ------------------------------------------------------------------------------------
-template <int WPB>
+template <int WPB, typename S = double>
 __global__ void __launch_bounds__(WPB * 32) k_adj_sweep(Dev<double> c, AdjBufs a, const int* cells,
                                                         int n, const double* r, double* y) {
     const int lane = threadIdx.x & 31;
@@ -748,24 +854,24 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_sweep(Dev<double> c, AdjBufs a
     const int i = cells[t];
     const int s0 = c.slot_off[i], s1 = c.slot_off[i + 1];
     const size_t NK = (size_t)c.N * c.Kp;
-    const double base = 1.0 / (c.cfl_imp * c.dt[i]) + 1.0 / a.tau[i];
+    const S base = (S)(1.0 / (c.cfl_imp * c.dt[i]) + 1.0 / a.tau[i]);
     for (int k = lane; k < c.K; k += 32) {
-        const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k];
-        double D = base, ag = 0.0, ah = 0.0;
+        const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k);
+        S D = base, ag = S(0), ah = S(0);
         for (int m = s0; m < s1; ++m) {
-            double un = dot_rn(ux, uy, uz, c.slot_n[m], c.slot_n[c.nnz + m], c.slot_n[2 * c.nnz + m]);
+            S un = dot_rn(ux, uy, uz, (S)c.slot_n[m], (S)c.slot_n[c.nnz + m], (S)c.slot_n[2 * c.nnz + m]);
             if (!c.slot_left[m]) un = -un;
-            if (!(un > 0.0)) continue;
-            D += c.slot_AV[m] * un;
+            if (!(un > S(0))) continue;
+            D += (S)c.slot_AV[m] * un;
             const int j = c.slot_nbr[m];
             if (j < 0) continue;
-            const double cf = a.slot_AVn[m] * un;
-            ag += cf * y[(size_t)j * c.Kp + k];
-            ah += cf * y[NK + (size_t)j * c.Kp + k];
+            const S cf = (S)a.slot_AVn[m] * un;
+            ag += cf * (S)y[(size_t)j * c.Kp + k];
+            ah += cf * (S)y[NK + (size_t)j * c.Kp + k];
         }
         const size_t o = (size_t)i * c.Kp + k;
-        y[o] = (r[o] + ag) / D;
-        y[NK + o] = (r[NK + o] + ah) / D;
+        y[o] = (double)(((S)r[o] + ag) / D);
+        y[NK + o] = (double)(((S)r[NK + o] + ah) / D);
     }
 }
 

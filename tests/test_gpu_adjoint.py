@@ -158,10 +158,12 @@ def test_autograd_function_gives_the_adjoint_gradient():
     assert _rel(p.grad.numpy(), dJdp) < 1e-12
 
 
-def test_adjoint_of_a_mixed_precision_context():
-    """A mixed context's adjoint is the FP64 adjoint at its (FP32-distribution) state:
-    VJP parity with the oracle at that state, and dJ/dp close to the FP64 context's
-    (the two steady states differ at the mixed-precision level)."""
+def test_adjoint_of_a_mixed_precision_context(monkeypatch):
+    """A mixed context's adjoint at its (FP32-distribution) state.  With FP64 arithmetic
+    (RYKOV_ADJ_FP64=1) the VJP equals the oracle's at that state to 1e-10; with the
+    default FP32 per-velocity arithmetic (compensated velocity sums) to 1e-5; the
+    FP32 adjoint solve gives dJ/dp within 1e-4 of the FP64 context's (the two steady
+    states differ at the mixed-precision level)."""
     wl = lid_farfield()
     sm = _solver_prec(wl, "mixed", 30)
     rc, n, res = sm.iterate(400, 1e-9)
@@ -170,12 +172,19 @@ def test_adjoint_of_a_mixed_precision_context():
     st = Steady(wl)
     xt = torch.as_tensor(x)
     v = np.random.default_rng(4).standard_normal(x.size)
-    out, pp = sm.vjp(v)
     ot, pt = st.vjp(xt, torch.as_tensor(v))
+    monkeypatch.setenv("RYKOV_ADJ_FP64", "1")
+    out, pp = sm.vjp(v)
     for a, b in zip(_blocks(st, out), _blocks(st, ot.numpy())):
         assert _rel(a, b) < TOL
-    it, rel, J, dJdp = sm.adjoint_solve("heat", max_iter=400, tol=1e-10)
-    assert rel <= 1e-10
+    assert _rel(pp, pt.numpy()) < TOL
+    monkeypatch.delenv("RYKOV_ADJ_FP64")
+    out32, pp32 = sm.vjp(v)
+    for a, b in zip(_blocks(st, out32), _blocks(st, ot.numpy())):
+        assert _rel(a, b) < 1e-5
+    assert _rel(pp32, pt.numpy()) < 1e-5
+    it, rel, J, dJdp = sm.adjoint_solve("heat", max_iter=400, tol=1e-6)
+    assert rel <= 1e-6
     s64 = _solver(wl, 30)
     s64.iterate(3000, 1e-13)
     _, _, J64, dJdp64 = s64.adjoint_solve("heat", max_iter=400, tol=1e-10)

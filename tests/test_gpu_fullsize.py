@@ -202,3 +202,26 @@ def test_sphere_mixed_converges_to_1e_6(sphere):
     s = _solver(sphere, "mixed")
     rc, n, res = s.iterate(300, tol=1e-6)
     assert rc == 0 and np.max(res) < 1e-6 and n < 300
+
+
+def test_mixed_adjoint_fp32_arithmetic_at_full_size(sphere, monkeypatch):
+    """The adjoint of the mixed sphere with FP32 per-velocity arithmetic against the same
+    context with FP64 arithmetic (RYKOV_ADJ_FP64=1): the heat objective, its gradient
+    and the VJP applied to that gradient agree to 1e-4 (normwise per block), dR/dp^T v
+    to 1e-4."""
+    s = _solver(sphere, "mixed")
+    s.iterate(150)
+    s.bind_adjoint(1)
+    monkeypatch.setenv("RYKOV_ADJ_FP64", "1")
+    J64, g64, dp64 = s.objective("heat")
+    out64, pp64 = s.vjp(g64)
+    monkeypatch.delenv("RYKOV_ADJ_FP64")
+    J32, g32, dp32 = s.objective("heat")
+    out32, pp32 = s.vjp(g64)
+    n1 = 2 * s.N * s.K
+    assert abs(J32 - J64) <= 1e-6 * abs(J64)
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    assert rel(g32, g64) < 1e-4 and rel(dp32, dp64) < 1e-4
+    for a, b in ((out32[:n1], out64[:n1]), (out32[n1:], out64[n1:])):
+        assert rel(a, b) < 1e-4
+    assert rel(pp32, pp64) < 1e-4
