@@ -275,6 +275,14 @@ static cudaError_t adj_apply(rk_ctx* ctx, AdjState& A, const double* v, double* 
     cudaStream_t s = ctx->stream;
     const int gc = rk::cdv(ctx->N, rk::ADJ_WPB);
     const bool f32 = adj_fp32(ctx);
+    if (f32) {
+        // the phi block of v rounded to FP32 once, into the upper half of the gradient
+        // adjoint buffer (FP32 arithmetic stores those adjoints in its lower half)
+        float* vf = reinterpret_cast<float*>(A.nbg) + 8 * (size_t)ctx->N * ctx->Kp;
+        rk::k_adj_downcast<<<1216, 256, 0, s>>>(v, vf, 2 * (size_t)ctx->N * ctx->Kp);
+        a.vphif = vf;
+        A.launches++;
+    }
     if (f32) rk::k_adj_cell<rk::ADJ_WPB, float><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a, 3);
     else rk::k_adj_cell<rk::ADJ_WPB, double><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, a, 3);
     A.launches += 4;

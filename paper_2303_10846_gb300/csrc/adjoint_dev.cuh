@@ -23,7 +23,11 @@
 
 namespace rk {
 
-constexpr int ADJ_FPAR = 12;     // per boundary face: dR/dp^T v (6), J, force (3), 2 spare
+constexpr int ADJ_FPAR = 12;
+// minimum resident blocks of the per-velocity adjoint kernels (register budget)
+#ifndef ADJ_MINB
+#define ADJ_MINB 1
+#endif     // per boundary face: dR/dp^T v (6), J, force (3), 2 spare
 
 struct AdjBufs {
     double *f0, *fbar;           // [2][F][Kp] phi(x_f - u s) and its adjoint
@@ -44,6 +48,7 @@ struct AdjBufs {
     // FP32 arithmetic of a mixed context: its FP32 velocity set and distributions
     const float *uf, *wf, *phif;
     const float* f0f;            // [2][F][Kp] the FP32 reconstruction (phi0 at the faces)
+    const float* vphif;          // [2][N][Kp] the phi block of v rounded to FP32
 };
 
 // per-velocity inputs in the arithmetic type S: FP32 arrays of a mixed context when S
@@ -57,6 +62,11 @@ template <typename S>
 __device__ __forceinline__ S wgt(const Dev<double>& c, const AdjBufs& a, int k) {
     if constexpr (sizeof(S) == 4) return a.wf[k];
     else return c.w[k];
+}
+template <typename S>
+__device__ __forceinline__ S vin(const AdjBufs& a, size_t o) {
+    if constexpr (sizeof(S) == 4) return a.vphif[o];
+    else return a.vphi[o];
 }
 template <typename S>
 __device__ __forceinline__ S dist(const Dev<double>& c, const AdjBufs& a, size_t o) {
@@ -179,7 +189,7 @@ __device__ __forceinline__ void eq_vjp(const EqS<S>& s, S om0, S om1, S del, S Z
 // flux part later); bit 1: write oW, oq.  One warp per cell.
 // ------------------------------------------------------------------------------------
 template <int WPB, typename S = double>
-__global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a, int mode) {
+__global__ void __launch_bounds__(WPB * 32, sizeof(S) == 4 ? ADJ_MINB : 1) k_adj_cell(Dev<double> c, AdjBufs a, int mode) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * WPB + (threadIdx.x >> 5);
     if (i >= c.N) return;
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_cell(Dev<double> c, AdjBufs a,
         const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k), w = wgt<S>(c, a, k);
         const size_t o = (size_t)i * c.Kp + k;
         const S g = dist<S>(c, a, o), h = dist<S>(c, a, NK + o);
-        const S vg = (S)a.vphi[o], vh = (S)a.vphi[NK + o];
+        const S vg = vin<S>(a, o), vh = vin<S>(a, NK + o);
         const S cx = ux - Us[0], cy = uy - Us[1], cz = uz - Us[2];
         const S c2 = cx * cx + cy * cy + cz * cz;
         const S cvt = cx * vqs[0] + cy * vqs[1] + cz * vqs[2];
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_residual(Dev<double> c, AdjBuf
 //   pass B    : adjoint of phi0, written to fbar
 // ------------------------------------------------------------------------------------
 template <int WPB, typename S = double>
-__global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, AdjBufs a) {
+__global__ void __launch_bounds__(WPB * 32, sizeof(S) == 4 ? ADJ_MINB : 1) k_adj_face_interior(Dev<double> c, AdjBufs a) {
     const int lane = threadIdx.x & 31;
     const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
     if (fi >= c.Fi) return;
@@ -425,8 +435,7 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
     const double ab = tau / (tau + s), bb = s / (tau + s), db = s / ((tau + s) * (tau + s));
     const double nx = c.fn[f], ny = c.fn[c.F + f], nz = c.fn[2 * c.F + f], A = c.fa[f];
     const double iVl = 1.0 / c.vol[cl], iVr = 1.0 / c.vol[cr];
-    const double* vgl = a.vphi + (size_t)cl * c.Kp;
-    const double* vgr = a.vphi + (size_t)cr * c.Kp;
+    const size_t ol = (size_t)cl * c.Kp, orr = (size_t)cr * c.Kp;   // rows of v at the two cells
     double acc[14];
     {
         const S nxs = (S)nx, nys = (S)ny, nzs = (S)nz, As = (S)A, iVls = (S)iVl, iVrs = (S)iVr;
@@ -435,8 +444,8 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
         for (int k = lane; k < c.K; k += 32) {
             const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k);
             const S wn = -As * dot_rn(ux, uy, uz, nxs, nys, nzs);
-            const S wgb = wn * ((S)vgl[k] * iVls - (S)vgr[k] * iVrs);
-            const S whb = wn * ((S)vgl[NK + k] * iVls - (S)vgr[NK + k] * iVrs);
+            const S wgb = wn * (vin<S>(a, ol + k) * iVls - vin<S>(a, orr + k) * iVrs);
+            const S whb = wn * (vin<S>(a, NK + ol + k) * iVls - vin<S>(a, NK + orr + k) * iVrs);
             S G, H, dd[13];
             eq_vjp<S>(st, om0, om1, del, ZS, ux, uy, uz, bbs * wgb, bbs * whb, dd, G, H);
 #pragma unroll
@@ -500,8 +509,8 @@ __global__ void __launch_bounds__(WPB * 32) k_adj_face_interior(Dev<double> c, A
     for (int k = lane; k < c.K; k += 32) {
         const S ux = vel<S>(c, a, 0, k), uy = vel<S>(c, a, 1, k), uz = vel<S>(c, a, 2, k), w = wgt<S>(c, a, k);
         const S wn = -As * dot_rn(ux, uy, uz, nxs, nys, nzs);
-        const S wgb = wn * ((S)vgl[k] * iVls - (S)vgr[k] * iVrs);
-        const S whb = wn * ((S)vgl[NK + k] * iVls - (S)vgr[NK + k] * iVrs);
+        const S wgb = wn * (vin<S>(a, ol + k) * iVls - vin<S>(a, orr + k) * iVrs);
+        const S whb = wn * (vin<S>(a, NK + ol + k) * iVls - vin<S>(a, NK + orr + k) * iVrs);
         const S cx = ux - Us[0], cy = uy - Us[1], cz = uz - Us[2];
         const S c2 = cx * cx + cy * cy + cz * cz;
         gb[k] = (double)(abs_ * wgb + w * (rbs + mbs[0] * ux + mbs[1] * uy + mbs[2] * uz +
@@ -649,7 +658,7 @@ __global__ void __launch_bounds__(BS) k_adj_face_boundary(Dev<double> c, AdjBufs
 // gave it, for the neighbours to gather.  One warp per cell.
 // ------------------------------------------------------------------------------------
 template <int WPB, typename S = double>
-__global__ void __launch_bounds__(WPB * 32) k_adj_gather(Dev<double> c, AdjBufs a) {
+__global__ void __launch_bounds__(WPB * 32, sizeof(S) == 4 ? ADJ_MINB : 1) k_adj_gather(Dev<double> c, AdjBufs a) {
     __shared__ int s_face[WPB][MAXF], s_nbr[WPB][MAXF], s_left[WPB][MAXF];
     __shared__ S s_lsq[WPB][3][MAXF], s_d[WPB][3][MAXF], s_n[WPB][3][MAXF], s_s[WPB][MAXF];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
