@@ -1,4 +1,5 @@
-// Device side of the adjoint of the steady residual operator (FP64).
+// Device side of the adjoint of the steady residual operator (FP64, or FP32 per-velocity
+// arithmetic for mixed-precision contexts).
 //
 // Unknowns X = (phi, W, q) of a steady state of the implicit iteration (Sec. 3.5 with
 // dphi = 0 and a zero macro increment), residual R(X; p) = (R_phi, R_W, R_q):

@@ -298,7 +298,7 @@ class Solver:
         self._check(self.L.rk_residual(self.h, _ptr(res)))
         return res
 
-    # ---- adjoint of the steady residual (FP64 solvers) ------------------------------
+    # ---- adjoint of the steady residual ---------------------------------------------
     def bind_adjoint(self, krylov_dim: int = 20):
         """Allocate (torch) and bind the adjoint workspace; krylov_dim = GMRES restart."""
         torch = self.torch
