@@ -9,7 +9,6 @@ anywhere, but creating a solver requires the compiled library and a CUDA device.
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 
