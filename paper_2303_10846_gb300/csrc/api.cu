@@ -36,6 +36,9 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     // middle, last sweep); the results are the same either way
     if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::atoi(v) & 7;
     if (const char* v = std::getenv("RYKOV_PRIO")) ctx->use_prio = std::strcmp(v, "0") != 0;
+    // RYKOV_MACRO_FP64=1: mixed contexts solve the macro PR-SGS in FP64 (as FP64
+    // contexts do) instead of the FP32 delta form
+    if (const char* v = std::getenv("RYKOV_MACRO_FP64")) ctx->use_macro32 = std::strcmp(v, "1") != 0;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
     std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
@@ -412,6 +415,7 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
         for (int64_t i = 0; i < N; ++i) maxs = std::max(maxs, ctx->slot_off[i + 1] - ctx->slot_off[i]);
         ctx->sched.maxs = maxs;
         ctx->sched.staged = (ctx->use_staged && rk::Launch<T>::micro_staged_smem(maxs) > 0) ? ctx->use_staged : 0;
+        ctx->sched.macro32 = (ctx->prec == RK_MIXED && ctx->use_macro32) ? 1 : 0;
         cudaGetLastError();
     }
     // zero the distribution-sized arrays once so that the K padding stays 0

@@ -1401,16 +1401,141 @@ __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cel
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Macro PR-SGS in FP32, delta form (mixed contexts)
+// ------------------------------------------------------------------------------------
+// The same point updates as macro_point, with the flux difference
+// G_ij(W_j + dW~_j) - G_ij(W_j^n) written in the increments themselves, so that FP32
+// loses nothing to cancellation.  With m = rho U, H = rho E + p, U_n = U.n (n scaled
+// by A/2V), ~ the current iterate and unmarked quantities those of W^n:
+//   dG_0 = dm.n,   dG_d = dm_d U_n + m~_d dU_n + dp n_d   (d = x, y, z),
+//   dG_4 = dH U_n + H~ dU_n,   dG_5 = d(rho E_rot) U_n + (rho E_rot)~ dU_n,
+//   dU = (dm - U d rho) / rho~,   dp = (2/5) (d(rho E) - (dm.U + m~.dU) / 2).
+// The constant part of every update, F_i (and for rho E_rot minus the source at W^n,
+// (p - rho E_rot)/(Z tau)), is formed in FP64 and rounded once; it vanishes with the
+// steady residual.  Every other FP32 rounding is relative to the increments, which
+// vanish too, so the converged state is that of the FP64 solve, and each iterate
+// differs from it by a relative 1e-6 or so of its own increment.
+// Records, float4 views of the FP64 macro buffers (which this form leaves unused):
+//   base  [N][3] in mPc: (U, H) | (m, rho E_rot) | (rho, rho E, p, 1/(Z tau))   at W^n
+//   delta [N][3] in mB:  (d rho, dm) | (d(rho E), d(rho E_rot), dp, 0) | (dU, 0)
+//   own   [N][2] in mDb: (F_0..3) | (F_4, F_5 - (p - rho E_rot)/(Z tau), 1/D, 1/(D + 1/(Z tau)))
+//   slot  [nnz]  in sG0: ((A/2V) n, A r/(2V)), position-ordered like pslot_nbr
+template <typename T>
+__global__ void k_macro_prep32(Dev<T> c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
+    const double cfl = c.iterp[0];
+    const double iv = 1.0 / c.vol[i];
+    double D = 1.0 / (cfl * c.dt[i]);
+    const int ps = c.pos_off[c.cell_pos[i]];
+    float4* sl = reinterpret_cast<float4*>(c.sG0);
+    for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
+        const int f = c.slot_face[m];
+        const size_t mp = (size_t)(ps + m - c.slot_off[i]);
+        const double c2 = 0.5 * c.fa[f] * iv * c.rf[f];
+        D += c2;
+        sl[mp] = make_float4((float)c.pslot_n[mp], (float)c.pslot_n[c.nnz + mp],
+                             (float)c.pslot_n[2 * c.nnz + mp], (float)c2);
+    }
+    const double* W = c.W + 6 * (size_t)i;
+    const Prim pr = prim_from_W(W, c.R);
+    const double izt = 1.0 / (c.Z * relax_time(c, pr.rho, pr.Ttr));
+    const double rho = W[0], ir = 1.0 / rho;
+    const double U[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
+    const double p = 0.4 * (W[4] - 0.5 * rho * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]));
+    const double* F = c.macroF + 6 * (size_t)i;
+    float4* base = reinterpret_cast<float4*>(c.mPc) + 3 * (size_t)i;
+    base[0] = make_float4((float)U[0], (float)U[1], (float)U[2], (float)(W[4] + p));
+    base[1] = make_float4((float)W[1], (float)W[2], (float)W[3], (float)W[5]);
+    base[2] = make_float4((float)rho, (float)W[4], (float)p, (float)izt);
+    float4* own = reinterpret_cast<float4*>(c.mDb) + 2 * (size_t)i;
+    own[0] = make_float4((float)F[0], (float)F[1], (float)F[2], (float)F[3]);
+    own[1] = make_float4((float)F[4], (float)(F[5] - (p - W[5]) * izt), (float)(1.0 / D),
+                         (float)(1.0 / (D + izt)));
+    float4* dl = reinterpret_cast<float4*>(c.mB) + 3 * (size_t)i;
+    dl[0] = dl[1] = dl[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, const int* col_cell, int lo, int n,
+                                                       int colour, int first_forward) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
+    if (t >= n) return;                           // whole lane group
+    const int g = (int)(threadIdx.x % MACRO_LANES);
+    const int p = lo + t, i = col_cell[p];
+    const float4* base = reinterpret_cast<const float4*>(c.mPc);
+    const float4* own = reinterpret_cast<const float4*>(c.mDb);
+    const float4* sl = reinterpret_cast<const float4*>(c.sG0);
+    float4* dl = reinterpret_cast<float4*>(c.mB);
+    float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (g == 0) {
+        const float4 a = own[2 * (size_t)i], b = own[2 * (size_t)i + 1];
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+    }
+    for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += MACRO_LANES) {
+        const int j = c.pslot_nbr[m];
+        if (j < 0 || (first_forward && c.pslot_ncol[m] > colour)) continue;
+        const float4 s = sl[m];
+        // the neighbour's increments are read through L2 (written by earlier launches)
+        const float4 d0 = __ldcg(dl + 3 * (size_t)j), d1 = __ldcg(dl + 3 * (size_t)j + 1),
+                     d2 = __ldcg(dl + 3 * (size_t)j + 2);
+        const float4 b0 = base[3 * (size_t)j], b1 = base[3 * (size_t)j + 1];
+        const float Un = b0.x * s.x + b0.y * s.y + b0.z * s.z;
+        const float dUn = d2.x * s.x + d2.y * s.y + d2.z * s.z;
+        const float dH = d1.x + d1.z;
+        o[0] += d0.y * s.x + d0.z * s.y + d0.w * s.z - s.w * d0.x;
+        o[1] += d0.y * Un + (b1.x + d0.y) * dUn + d1.z * s.x - s.w * d0.y;
+        o[2] += d0.z * Un + (b1.y + d0.z) * dUn + d1.z * s.y - s.w * d0.z;
+        o[3] += d0.w * Un + (b1.z + d0.w) * dUn + d1.z * s.z - s.w * d0.w;
+        o[4] += dH * Un + (b0.w + dH) * dUn - s.w * d1.x;
+        o[5] += d1.y * Un + (b1.w + d1.y) * dUn - s.w * d1.y;
+    }
+    if (MACRO_LANES > 1) {
+        const unsigned mask = MACRO_LANES == 32 ? 0xffffffffu
+                                                : ((1u << MACRO_LANES) - 1u) << ((threadIdx.x & 31) & ~(MACRO_LANES - 1));
+#pragma unroll
+        for (int off = 1; off < MACRO_LANES; off <<= 1)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) o[q] += __shfl_xor_sync(mask, o[q], off);
+    }
+    if (g != 0) return;
+    const float4 b0 = base[3 * (size_t)i], b1 = base[3 * (size_t)i + 1], b2 = base[3 * (size_t)i + 2];
+    const float4 ob = own[2 * (size_t)i + 1];
+    // dp of the current iterate: the implicit part of the rotational source
+    const float dpi = __ldcg(reinterpret_cast<const float*>(dl + 3 * (size_t)i + 1) + 2);
+    float cand[6];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) cand[q] = -o[q] * ob.z;
+    cand[5] = (dpi * b2.w - o[5]) * ob.w;
+    // the candidate iterate, skipped if not admissible (rho, T_tr or T_rot <= 0)
+    const float rho = b2.x + cand[0];
+    if (!(rho > 0.f)) return;
+    const float mx = b1.x + cand[1], my = b1.y + cand[2], mz = b1.z + cand[3];
+    const float dUx = (cand[1] - b0.x * cand[0]) / rho, dUy = (cand[2] - b0.y * cand[0]) / rho,
+                dUz = (cand[3] - b0.z * cand[0]) / rho;
+    const float dke = 0.5f * (cand[1] * b0.x + cand[2] * b0.y + cand[3] * b0.z + mx * dUx + my * dUy + mz * dUz);
+    const float ke = 0.5f * (mx * (b0.x + dUx) + my * (b0.y + dUy) + mz * (b0.z + dUz));
+    const float er = b1.w + cand[5];
+    if (!((b2.y + cand[4]) - ke - er > 0.f && er > 0.f)) return;
+    __stcg(dl + 3 * (size_t)i, make_float4(cand[0], cand[1], cand[2], cand[3]));
+    __stcg(dl + 3 * (size_t)i + 1, make_float4(cand[4], cand[5], 0.4f * (cand[4] - dke), 0.f));
+    __stcg(dl + 3 * (size_t)i + 2, make_float4(dUx, dUy, dUz, 0.f));
+}
+
 // W~ = W^n + dW~, tau~ and the per-cell record of the micro sweeps: constants of the
 // predicted equilibrium phi~* built from (W~, q^n) (reading: the prediction gives no
-// heat flux, so the last Step-6 value is used), 1/tau~, and 1/dt + 1/tau~.
+// heat flux, so the last Step-6 value is used), 1/tau~, and 1/dt + 1/tau~.  dW~ is
+// the FP64 iterate, or with m32 the first six floats of the FP32 delta record.
 template <typename T>
-__global__ void k_macro_finish(Dev<T> c) {
+__global__ void k_macro_finish(Dev<T> c, int m32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
     const double cfl = c.iterp[0];
     double* Wt = c.Wt + 6 * (size_t)i;
-    for (int m = 0; m < 6; ++m) Wt[m] = c.W[6 * (size_t)i + m] + c.dW[6 * (size_t)i + m];
+    const float* d32 = reinterpret_cast<const float*>(c.mB) + 12 * (size_t)i;
+    for (int m = 0; m < 6; ++m)
+        Wt[m] = c.W[6 * (size_t)i + m] + (m32 ? (double)d32[m] : c.dW[6 * (size_t)i + m]);
     const Prim p = prim_from_W(Wt, c.R);
     const double tau = relax_time(c, p.rho, p.Ttr);
     c.taut[i] = tau;

@@ -40,6 +40,7 @@ struct Sched {
     int maxs = 0;                   // most faces of one cell
     int staged = 0;                 // micro sweeps with staged (asynchronous) row loads:
                                     // bit 0 first sweep, bit 1 middle sweeps, bit 2 last
+    int macro32 = 0;                // macro PR-SGS in FP32 delta form (mixed contexts)
 };
 
 template <typename T>

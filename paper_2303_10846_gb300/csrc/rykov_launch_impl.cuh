@@ -89,9 +89,30 @@ template <typename T>
 cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, int n_macro,
                              Prof& pf) {
     pf.begin(4, s);
+    const int C = (int)sc.col_off.size() - 1;
+    if (sc.macro32) {
+        // FP32 delta form (mixed contexts): per-colour launches
+        k_macro_prep32<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
+        pf.launches += 1;
+        for (int it = 0; it < n_macro; ++it) {
+            for (int dir = 0; dir < 2; ++dir) {
+                for (int cc = 0; cc < C; ++cc) {
+                    const int col = dir == 0 ? cc : C - 1 - cc;
+                    const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
+                    if (!n) continue;
+                    k_macro_sweep32<T><<<cdiv((long long)n * MACRO_LANES, 128), 128, 0, s>>>(
+                        d, sc.col_cell, lo, n, col, it == 0 && dir == 0);
+                    pf.launches += 1;
+                }
+            }
+        }
+        k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d, 1);
+        pf.end(s);
+        pf.launches += 1;
+        return cudaGetLastError();
+    }
     k_macro_prep<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
     pf.launches += 1;
-    const int C = (int)sc.col_off.size() - 1;
     bool done = false;
     if (sc.coop_grid > 0 && n_macro > 0) {
         // all sweeps in one cooperative launch (grid barriers between colours)
@@ -124,7 +145,7 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             }
         }
     }
-    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
+    k_macro_finish<T><<<cdiv(d.N, 128), 128, 0, s>>>(d, 0);
     pf.end(s);
     pf.launches += 1;
     return cudaGetLastError();

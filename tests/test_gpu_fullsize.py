@@ -162,7 +162,9 @@ def test_full_size_iterations_are_bitwise_repeatable(sphere):
 
 def test_cooperative_macro_solve_is_bitwise_identical_at_full_size(sphere, monkeypatch):
     """The cooperative macro PR-SGS (grid barriers between colour phases) gives the same
-    iterates as the per-colour launches on the full sphere."""
+    iterates as the per-colour launches on the full sphere (mixed context with the FP64
+    macro solve, the one that has a cooperative form)."""
+    monkeypatch.setenv("RYKOV_MACRO_FP64", "1")
     a = _solver(sphere, "mixed")
     a.iterate(15)
     Wa, qa, _ = a.moments()
@@ -202,6 +204,26 @@ def test_sphere_mixed_converges_to_1e_6(sphere):
     s = _solver(sphere, "mixed")
     rc, n, res = s.iterate(300, tol=1e-6)
     assert rc == 0 and np.max(res) < 1e-6 and n < 300
+
+
+def test_macro_fp32_converges_like_the_fp64_macro_solve(sphere, monkeypatch):
+    """The FP32 delta-form macro solve of mixed contexts against the FP64 one, both from
+    the initial field to the residual 1e-6: the same number of iterations within 3, and
+    the converged wall pressure, heat flux and C_D within 1e-5 (relative to their
+    largest values)."""
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("RYKOV_MACRO_FP64", flag)
+        s = _solver(sphere, "mixed")
+        rc, n, res = s.iterate(300, tol=1e-6)
+        assert rc == 0 and np.max(res) < 1e-6
+        out.append((n, s.surface()[0], s.aero()))
+        s.close()
+    (n64, p64, a64), (n32, p32, a32) = out
+    assert abs(n32 - n64) <= 3
+    for c in (0, 4):                                 # p_w, q_w
+        assert np.max(np.abs(p32[:, c] - p64[:, c])) <= 1e-5 * np.max(np.abs(p64[:, c]))
+    assert abs(a32[6] - a64[6]) <= 1e-5 * abs(a64[6])
 
 
 def test_mixed_adjoint_fp32_arithmetic_at_full_size(sphere, monkeypatch):

@@ -121,9 +121,9 @@ def test_set_state_round_trip_and_restart_is_deterministic():
 
 
 def test_mixed_precision_tracks_fp64_cavity():
-    """Mixed mode (FP32 distributions, compensated FP64 reductions, FP64 macro
-    solve) against the FP64 oracle on the converged cavity: wall pressure, shear,
-    heat flux and force within 1e-5 relative."""
+    """Mixed mode (FP32 distributions, compensated FP64 reductions, FP32 delta-form
+    macro solve) against the FP64 oracle on the converged cavity: wall pressure,
+    shear, heat flux and force within 1e-5 relative."""
     wl = I.cavity_workload()
     o = O.Oracle(wl)
     o.iterate(120)
@@ -139,6 +139,50 @@ def test_mixed_precision_tracks_fp64_cavity():
     assert _rel(per[:, 4], per_o[:, 4]) < 1e-4            # wall heat flux (small, ~1e-4 of p)
     scale = (wl.mesh.face_area[wl.mesh.face_cell[:, 1] < 0] * per_o[:, 0]).sum()
     assert np.abs(force - force_o).max() < 1e-5 * scale
+
+
+@pytest.mark.parametrize("name", ["cavity4", "tet", "tet_k_ragged", "tet_sutherland"])
+def test_macro_fp32_delta_form_matches_fp64_macro_solve(name, monkeypatch):
+    """Mixed contexts solve the macro PR-SGS (Eq. implicit_mac_equ_fin) in FP32 in delta
+    form.  From the same inputs (the first iteration: every step before the macro
+    solve is bit-identical) its increment W~ - W^n agrees with the FP64 solve's (the one
+    FP64 contexts run, pinned to the oracle by test_step_by_step_fp64) to 2e-5 of the
+    largest increment of each variable, and tau~ to 1e-6.  A dropped or mis-signed
+    term of the flux difference shows up at the 1e-2 level."""
+    from paper_2303_10846_gb300 import rykov as RK
+    wl = WORKLOADS[name]()
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("RYKOV_MACRO_FP64", flag)
+        s = _solver(wl, "mixed")
+        for st in (RK.STEP_RECON, RK.STEP_FACES, RK.STEP_FLUXES, RK.STEP_MACRO):
+            s.step(st)
+        out.append((s.debug_get("W"), s.debug_get("WT"), s.debug_get("TAUT")))
+        s.close()
+    (W, Wt64, tau64), (W2, Wt32, tau32) = out
+    assert np.array_equal(W, W2)
+    d64, d32 = Wt64 - W, Wt32 - W
+    for v in range(6):
+        # (a variable that the problem's symmetry keeps constant: on the scale of 1e-10 W)
+        scale = max(np.max(np.abs(d64[:, v])), 1e-10 * np.max(np.abs(W[:, v])))
+        assert np.max(np.abs(d32[:, v] - d64[:, v])) <= 2e-5 * scale, f"variable {v}"
+    assert _rel(tau32, tau64) < 1e-6
+
+
+def test_macro_fp32_tracks_fp64_macro_over_iterations(monkeypatch):
+    """Ten iterations of the tetrahedral case in mixed precision with either macro
+    solve: the moments stay within 1e-6 (relative to their largest values)."""
+    wl = WORKLOADS["tet"]()
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("RYKOV_MACRO_FP64", flag)
+        s = _solver(wl, "mixed", debug=False)
+        rc, n, res = s.iterate(10)
+        assert rc == 0
+        out.append(s.moments()[:2])
+        s.close()
+    assert _rel(out[1][0], out[0][0]) < 1e-6
+    assert _rel(out[1][1], out[0][1]) < 1e-5
 
 
 def test_invalid_inputs_are_rejected():
