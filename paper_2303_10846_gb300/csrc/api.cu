@@ -39,6 +39,8 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     // RYKOV_MACRO_FP64=1: mixed contexts solve the macro PR-SGS in FP64 (as FP64
     // contexts do) instead of the FP32 delta form
     if (const char* v = std::getenv("RYKOV_MACRO_FP64")) ctx->use_macro32 = std::strcmp(v, "1") != 0;
+    // RYKOV_PDL=0: the FP32 macro phases as plain launches (same results)
+    if (const char* v = std::getenv("RYKOV_PDL")) ctx->use_pdl = std::strcmp(v, "0") != 0;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
     std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
@@ -416,6 +418,7 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
         ctx->sched.maxs = maxs;
         ctx->sched.staged = (ctx->use_staged && rk::Launch<T>::micro_staged_smem(maxs) > 0) ? ctx->use_staged : 0;
         ctx->sched.macro32 = (ctx->prec == RK_MIXED && ctx->use_macro32) ? 1 : 0;
+        ctx->sched.pdl = ctx->use_pdl ? 1 : 0;
         cudaGetLastError();
     }
     // zero the distribution-sized arrays once so that the K padding stays 0

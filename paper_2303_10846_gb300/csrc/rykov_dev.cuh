@@ -1416,11 +1416,14 @@ __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cel
 // steady residual.  Every other FP32 rounding is relative to the increments, which
 // vanish too, so the converged state is that of the FP64 solve, and each iterate
 // differs from it by a relative 1e-6 or so of its own increment.
-// Records, float4 views of the FP64 macro buffers (which this form leaves unused):
+// Records, float4 views of the FP64 macro buffers (which this form leaves unused),
+// indexed by the cell's colour position (cell_pos), so that a point update reads its
+// own records without first loading its cell index and one colour's are contiguous:
 //   base  [N][3] in mPc: (U, H) | (m, rho E_rot) | (rho, rho E, p, 1/(Z tau))   at W^n
 //   delta [N][3] in mB:  (d rho, dm) | (d(rho E), d(rho E_rot), dp, 0) | (dU, 0)
 //   own   [N][2] in mDb: (F_0..3) | (F_4, F_5 - (p - rho E_rot)/(Z tau), 1/D, 1/(D + 1/(Z tau)))
-//   slot  [nnz]  in sG0: ((A/2V) n, A r/(2V)), position-ordered like pslot_nbr
+//   slot  [nnz]  in sG0: ((A/2V) n, A r/(2V)), position-ordered like pslot_nbr, then
+//         [nnz] int2 after them: (neighbour's colour position or -1, its colour)
 template <typename T>
 __global__ void k_macro_prep32(Dev<T> c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1428,8 +1431,9 @@ __global__ void k_macro_prep32(Dev<T> c) {
     const double cfl = c.iterp[0];
     const double iv = 1.0 / c.vol[i];
     double D = 1.0 / (cfl * c.dt[i]);
-    const int ps = c.pos_off[c.cell_pos[i]];
+    const int pi = c.cell_pos[i], ps = c.pos_off[pi];
     float4* sl = reinterpret_cast<float4*>(c.sG0);
+    int2* si = reinterpret_cast<int2*>(sl + c.nnz);
     for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
         const int f = c.slot_face[m];
         const size_t mp = (size_t)(ps + m - c.slot_off[i]);
@@ -1437,6 +1441,8 @@ __global__ void k_macro_prep32(Dev<T> c) {
         D += c2;
         sl[mp] = make_float4((float)c.pslot_n[mp], (float)c.pslot_n[c.nnz + mp],
                              (float)c.pslot_n[2 * c.nnz + mp], (float)c2);
+        const int j = c.pslot_nbr[mp];
+        si[mp] = make_int2(j >= 0 ? c.cell_pos[j] : -1, c.pslot_ncol[mp]);
     }
     const double* W = c.W + 6 * (size_t)i;
     const Prim pr = prim_from_W(W, c.R);
@@ -1445,37 +1451,51 @@ __global__ void k_macro_prep32(Dev<T> c) {
     const double U[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
     const double p = 0.4 * (W[4] - 0.5 * rho * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]));
     const double* F = c.macroF + 6 * (size_t)i;
-    float4* base = reinterpret_cast<float4*>(c.mPc) + 3 * (size_t)i;
+    float4* base = reinterpret_cast<float4*>(c.mPc) + 3 * (size_t)pi;
     base[0] = make_float4((float)U[0], (float)U[1], (float)U[2], (float)(W[4] + p));
     base[1] = make_float4((float)W[1], (float)W[2], (float)W[3], (float)W[5]);
     base[2] = make_float4((float)rho, (float)W[4], (float)p, (float)izt);
-    float4* own = reinterpret_cast<float4*>(c.mDb) + 2 * (size_t)i;
+    float4* own = reinterpret_cast<float4*>(c.mDb) + 2 * (size_t)pi;
     own[0] = make_float4((float)F[0], (float)F[1], (float)F[2], (float)F[3]);
     own[1] = make_float4((float)F[4], (float)(F[5] - (p - W[5]) * izt), (float)(1.0 / D),
                          (float)(1.0 / (D + izt)));
-    float4* dl = reinterpret_cast<float4*>(c.mB) + 3 * (size_t)i;
+    float4* dl = reinterpret_cast<float4*>(c.mB) + 3 * (size_t)pi;
     dl[0] = dl[1] = dl[2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Launched with programmatic stream serialisation: each phase waits for the previous
+// one to complete, its writes visible, before it reads anything (griddepcontrol.wait),
+// and only then lets the next one be launched (griddepcontrol.launch_dependents), so
+// that the launch latency of the next colour overlaps this one while at most one phase
+// waits ahead.  Both are no-ops in a plain launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, const int* col_cell, int lo, int n,
-                                                       int colour, int first_forward) {
+__global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, int lo, int n, int colour,
+                                                       int first_forward) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
     if (t >= n) return;                           // whole lane group
     const int g = (int)(threadIdx.x % MACRO_LANES);
-    const int p = lo + t, i = col_cell[p];
+    const int p = lo + t;                         // colour position of the cell
     const float4* base = reinterpret_cast<const float4*>(c.mPc);
     const float4* own = reinterpret_cast<const float4*>(c.mDb);
     const float4* sl = reinterpret_cast<const float4*>(c.sG0);
+    const int2* si = reinterpret_cast<const int2*>(sl + c.nnz);
     float4* dl = reinterpret_cast<float4*>(c.mB);
     float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (g == 0) {
-        const float4 a = own[2 * (size_t)i], b = own[2 * (size_t)i + 1];
+        const float4 a = own[2 * (size_t)p], b = own[2 * (size_t)p + 1];
         o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
     }
     for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += MACRO_LANES) {
-        const int j = c.pslot_nbr[m];
-        if (j < 0 || (first_forward && c.pslot_ncol[m] > colour)) continue;
+        const int2 nb = si[m];
+        const int j = nb.x;
+        if (j < 0 || (first_forward && nb.y > colour)) continue;
         const float4 s = sl[m];
         // the neighbour's increments are read through L2 (written by earlier launches)
         const float4 d0 = __ldcg(dl + 3 * (size_t)j), d1 = __ldcg(dl + 3 * (size_t)j + 1),
@@ -1500,10 +1520,11 @@ __global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, const int* col_
             for (int q = 0; q < 6; ++q) o[q] += __shfl_xor_sync(mask, o[q], off);
     }
     if (g != 0) return;
-    const float4 b0 = base[3 * (size_t)i], b1 = base[3 * (size_t)i + 1], b2 = base[3 * (size_t)i + 2];
-    const float4 ob = own[2 * (size_t)i + 1];
+    const size_t i = (size_t)p;
+    const float4 b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
+    const float4 ob = own[2 * i + 1];
     // dp of the current iterate: the implicit part of the rotational source
-    const float dpi = __ldcg(reinterpret_cast<const float*>(dl + 3 * (size_t)i + 1) + 2);
+    const float dpi = __ldcg(reinterpret_cast<const float*>(dl + 3 * i + 1) + 2);
     float cand[6];
 #pragma unroll
     for (int q = 0; q < 5; ++q) cand[q] = -o[q] * ob.z;
@@ -1518,22 +1539,22 @@ __global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, const int* col_
     const float ke = 0.5f * (mx * (b0.x + dUx) + my * (b0.y + dUy) + mz * (b0.z + dUz));
     const float er = b1.w + cand[5];
     if (!((b2.y + cand[4]) - ke - er > 0.f && er > 0.f)) return;
-    __stcg(dl + 3 * (size_t)i, make_float4(cand[0], cand[1], cand[2], cand[3]));
-    __stcg(dl + 3 * (size_t)i + 1, make_float4(cand[4], cand[5], 0.4f * (cand[4] - dke), 0.f));
-    __stcg(dl + 3 * (size_t)i + 2, make_float4(dUx, dUy, dUz, 0.f));
+    __stcg(dl + 3 * i, make_float4(cand[0], cand[1], cand[2], cand[3]));
+    __stcg(dl + 3 * i + 1, make_float4(cand[4], cand[5], 0.4f * (cand[4] - dke), 0.f));
+    __stcg(dl + 3 * i + 2, make_float4(dUx, dUy, dUz, 0.f));
 }
 
 // W~ = W^n + dW~, tau~ and the per-cell record of the micro sweeps: constants of the
 // predicted equilibrium phi~* built from (W~, q^n) (reading: the prediction gives no
 // heat flux, so the last Step-6 value is used), 1/tau~, and 1/dt + 1/tau~.  dW~ is
-// the FP64 iterate, or with m32 the first six floats of the FP32 delta record.
+// the FP64 iterate, or with m32 the first six floats of the cell's FP32 delta record.
 template <typename T>
 __global__ void k_macro_finish(Dev<T> c, int m32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
     const double cfl = c.iterp[0];
     double* Wt = c.Wt + 6 * (size_t)i;
-    const float* d32 = reinterpret_cast<const float*>(c.mB) + 12 * (size_t)i;
+    const float* d32 = reinterpret_cast<const float*>(c.mB) + (m32 ? 12 * (size_t)c.cell_pos[i] : 0);
     for (int m = 0; m < 6; ++m)
         Wt[m] = c.W[6 * (size_t)i + m] + (m32 ? (double)d32[m] : c.dW[6 * (size_t)i + m]);
     const Prim p = prim_from_W(Wt, c.R);

@@ -41,6 +41,8 @@ struct Sched {
     int staged = 0;                 // micro sweeps with staged (asynchronous) row loads:
                                     // bit 0 first sweep, bit 1 middle sweeps, bit 2 last
     int macro32 = 0;                // macro PR-SGS in FP32 delta form (mixed contexts)
+    int pdl = 1;                    // its colour phases launched with programmatic
+                                    // stream serialisation
 };
 
 template <typename T>

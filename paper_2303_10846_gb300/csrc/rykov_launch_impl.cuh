@@ -91,17 +91,28 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
     pf.begin(4, s);
     const int C = (int)sc.col_off.size() - 1;
     if (sc.macro32) {
-        // FP32 delta form (mixed contexts): per-colour launches
+        // FP32 delta form (mixed contexts): per-colour launches, each overlapping the
+        // launch of the next (programmatic stream serialisation) unless sc.pdl is 0
         k_macro_prep32<T><<<cdiv(d.N, 128), 128, 0, s>>>(d);
         pf.launches += 1;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
         for (int it = 0; it < n_macro; ++it) {
             for (int dir = 0; dir < 2; ++dir) {
                 for (int cc = 0; cc < C; ++cc) {
                     const int col = dir == 0 ? cc : C - 1 - cc;
                     const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
                     if (!n) continue;
-                    k_macro_sweep32<T><<<cdiv((long long)n * MACRO_LANES, 128), 128, 0, s>>>(
-                        d, sc.col_cell, lo, n, col, it == 0 && dir == 0);
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3((unsigned)cdiv((long long)n * MACRO_LANES, 128));
+                    cfg.blockDim = dim3(128);
+                    cfg.stream = s;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = sc.pdl ? 1 : 0;
+                    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_macro_sweep32<T>, d, lo, n, col,
+                                                             (int)(it == 0 && dir == 0));
+                    if (e != cudaSuccess) return e;
                     pf.launches += 1;
                 }
             }

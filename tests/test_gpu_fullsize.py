@@ -175,6 +175,19 @@ def test_cooperative_macro_solve_is_bitwise_identical_at_full_size(sphere, monke
     assert np.array_equal(Wa, Wb) and np.array_equal(qa, qb)
 
 
+def test_macro_phase_launch_overlap_is_bitwise_identical_at_full_size(sphere, monkeypatch):
+    """The FP32 macro phases launched with and without programmatic serialisation
+    (RYKOV_PDL) give the same iterates on the full sphere."""
+    out = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("RYKOV_PDL", flag)
+        s = _solver(sphere, "mixed")
+        s.iterate(15)
+        out.append(s.moments()[:2])
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_staged_micro_sweeps_are_bitwise_identical_at_full_size(sphere, monkeypatch):
     """Staged and direct row loads in the micro sweeps give the same iterates on the
     full sphere (mixed precision, the bench configuration)."""

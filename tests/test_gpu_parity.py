@@ -193,18 +193,21 @@ def test_invalid_inputs_are_rejected():
         Solver(wl, "fp64")
 
 
-@pytest.mark.parametrize("env", [{"RYKOV_COOP": "1"}, {"RYKOV_GRAPH": "0"}])
-def test_launch_schemes_give_identical_results(env, monkeypatch):
-    """The cooperative macro solve (one launch, grid barriers between colours) and
-    the CUDA graph of an iteration follow the same order and arithmetic as per-colour
-    direct launches: the iterates agree bit for bit."""
+@pytest.mark.parametrize("prec,env", [("fp64", {"RYKOV_COOP": "1"}), ("fp64", {"RYKOV_GRAPH": "0"}),
+                                      ("mixed", {"RYKOV_GRAPH": "0"}), ("mixed", {"RYKOV_PDL": "0"}),
+                                      ("mixed", {"RYKOV_PDL": "0", "RYKOV_GRAPH": "0"})])
+def test_launch_schemes_give_identical_results(prec, env, monkeypatch):
+    """The cooperative macro solve (one launch, grid barriers between colours), the
+    CUDA graph of an iteration and the programmatic serialisation of the FP32 macro
+    phases follow the same order and arithmetic as per-colour direct launches: the
+    iterates agree bit for bit."""
     wl = TW.tiny_tet(lim=1, first_order_iters=1, cfl_imp=20.0)
-    a = _solver(wl, debug=False)
+    a = _solver(wl, prec, debug=False)
     a.iterate(4)
     Wa, qa, _ = a.moments()
     for k, v in env.items():
         monkeypatch.setenv(k, v)
-    b = _solver(wl, debug=False)
+    b = _solver(wl, prec, debug=False)
     b.iterate(4)
     Wb, qb, _ = b.moments()
     assert np.array_equal(Wa, Wb) and np.array_equal(qa, qb)
