@@ -88,7 +88,22 @@ typedef struct rk_ctx rk_ctx;
 int rk_version(void);
 
 /* Create a context of the given precision whose work goes to `cuda_stream`
- * (a cudaStream_t cast to uintptr_t; 0 = legacy default stream). */
+ * (a cudaStream_t cast to uintptr_t; 0 = legacy default stream).
+ * Arithmetic: RK_FP64 computes everything in FP64.  RK_MIXED stores the
+ * distributions in FP32 and computes per velocity in FP32, with compensated sums
+ * over the velocities combined in FP64, FP64 moments, interface states and
+ * compensation (Step 6), and the macro PR-SGS of Step 4 in FP32 in delta form: its
+ * constant part is formed in FP64 and every FP32 rounding is relative to the
+ * increment, so the converged state is the FP64 solve's.
+ * Environment switches read here (results unchanged unless noted):
+ *   RYKOV_GRAPH=0       no CUDA graph of an iteration;
+ *   RYKOV_COOP=1        cooperative launch of the FP64 macro PR-SGS;
+ *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4);
+ *   RYKOV_PRIO=0        no stream priorities in the graph;
+ *   RYKOV_PDL=0         FP32 macro phases without programmatic serialisation;
+ *   RYKOV_MACRO_FP64=1  RK_MIXED contexts run the FP64 macro PR-SGS (iterates differ
+ *                       by the rounding of the FP32 solve, ~1e-6 of the increment);
+ *   RYKOV_ADJ_FP64=1    RK_MIXED adjoint in FP64 (see the adjoint section). */
 int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream);
 int rk_destroy(rk_ctx* ctx);
 const char* rk_last_error(const rk_ctx* ctx);
