@@ -419,6 +419,12 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
         ctx->sched.staged = (ctx->use_staged && rk::Launch<T>::micro_staged_smem(maxs) > 0) ? ctx->use_staged : 0;
         ctx->sched.macro32 = (ctx->prec == RK_MIXED && ctx->use_macro32) ? 1 : 0;
         ctx->sched.pdl = ctx->use_pdl ? 1 : 0;
+        // RYKOV_MACRO_LANES=1|2|4: threads per cell of the FP32 macro phases, each taking
+        // every L-th face (default 4: one face each on tetrahedra)
+        if (const char* v = std::getenv("RYKOV_MACRO_LANES")) {
+            const int l = std::atoi(v);
+            ctx->sched.macro_lanes = (l == 1 || l == 2) ? l : 4;
+        }
         cudaGetLastError();
     }
     // zero the distribution-sized arrays once so that the K padding stays 0

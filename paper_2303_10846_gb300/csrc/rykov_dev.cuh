@@ -1473,14 +1473,16 @@ __device__ __forceinline__ void pdl_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <typename T>
+// LN threads per cell, each taking every LN-th face, the partial sums combined by a
+// butterfly (every lane of the group ends with the same bits; lane 0 stores).
+template <typename T, int LN>
 __global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, int lo, int n, int colour,
                                                        int first_forward) {
     pdl_wait();
     pdl_launch_dependents();
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) / LN;
     if (t >= n) return;                           // whole lane group
-    const int g = (int)(threadIdx.x % MACRO_LANES);
+    const int g = (int)(threadIdx.x % LN);
     const int p = lo + t;                         // colour position of the cell
     const float4* base = reinterpret_cast<const float4*>(c.mPc);
     const float4* own = reinterpret_cast<const float4*>(c.mDb);
@@ -1492,7 +1494,7 @@ __global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, int lo, int n, 
         const float4 a = own[2 * (size_t)p], b = own[2 * (size_t)p + 1];
         o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
     }
-    for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += MACRO_LANES) {
+    for (int m = c.pos_off[p] + g; m < c.pos_off[p + 1]; m += LN) {
         const int2 nb = si[m];
         const int j = nb.x;
         if (j < 0 || (first_forward && nb.y > colour)) continue;
@@ -1511,11 +1513,10 @@ __global__ void __launch_bounds__(128) k_macro_sweep32(Dev<T> c, int lo, int n, 
         o[4] += dH * Un + (b0.w + dH) * dUn - s.w * d1.x;
         o[5] += d1.y * Un + (b1.w + d1.y) * dUn - s.w * d1.y;
     }
-    if (MACRO_LANES > 1) {
-        const unsigned mask = MACRO_LANES == 32 ? 0xffffffffu
-                                                : ((1u << MACRO_LANES) - 1u) << ((threadIdx.x & 31) & ~(MACRO_LANES - 1));
+    if (LN > 1) {
+        const unsigned mask = LN == 32 ? 0xffffffffu : ((1u << LN) - 1u) << ((threadIdx.x & 31) & ~(LN - 1));
 #pragma unroll
-        for (int off = 1; off < MACRO_LANES; off <<= 1)
+        for (int off = 1; off < LN; off <<= 1)
 #pragma unroll
             for (int q = 0; q < 6; ++q) o[q] += __shfl_xor_sync(mask, o[q], off);
     }

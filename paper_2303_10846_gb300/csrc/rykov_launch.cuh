@@ -43,6 +43,7 @@ struct Sched {
     int macro32 = 0;                // macro PR-SGS in FP32 delta form (mixed contexts)
     int pdl = 1;                    // its colour phases launched with programmatic
                                     // stream serialisation
+    int macro_lanes = 4;            // threads per cell of the FP32 macro phases (1, 2, 4)
 };
 
 template <typename T>

@@ -104,14 +104,18 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
                     const int col = dir == 0 ? cc : C - 1 - cc;
                     const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
                     if (!n) continue;
+                    const int ln = sc.macro_lanes;
                     cudaLaunchConfig_t cfg = {};
-                    cfg.gridDim = dim3((unsigned)cdiv((long long)n * MACRO_LANES, 128));
+                    cfg.gridDim = dim3((unsigned)cdiv((long long)n * ln, 128));
                     cfg.blockDim = dim3(128);
                     cfg.stream = s;
                     cfg.attrs = attr;
                     cfg.numAttrs = sc.pdl ? 1 : 0;
-                    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_macro_sweep32<T>, d, lo, n, col,
-                                                             (int)(it == 0 && dir == 0));
+                    const int ff = (int)(it == 0 && dir == 0);
+                    const cudaError_t e =
+                        ln == 1 ? cudaLaunchKernelEx(&cfg, k_macro_sweep32<T, 1>, d, lo, n, col, ff)
+                        : ln == 4 ? cudaLaunchKernelEx(&cfg, k_macro_sweep32<T, 4>, d, lo, n, col, ff)
+                                  : cudaLaunchKernelEx(&cfg, k_macro_sweep32<T, 2>, d, lo, n, col, ff);
                     if (e != cudaSuccess) return e;
                     pf.launches += 1;
                 }

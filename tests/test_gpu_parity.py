@@ -169,6 +169,26 @@ def test_macro_fp32_delta_form_matches_fp64_macro_solve(name, monkeypatch):
     assert _rel(tau32, tau64) < 1e-6
 
 
+@pytest.mark.parametrize("lanes", ["1", "2"])
+def test_macro_fp32_lane_counts_agree(lanes, monkeypatch):
+    """The FP32 macro phases with 1 or 2 threads per cell instead of 4 (another order of
+    the face sums): the increments agree to 1e-5 of the largest after one macro solve."""
+    from paper_2303_10846_gb300 import rykov as RK
+    wl = WORKLOADS["tet_k_ragged"]()
+    out = []
+    for flag in ("4", lanes):
+        monkeypatch.setenv("RYKOV_MACRO_LANES", flag)
+        s = _solver(wl, "mixed")
+        for st in (RK.STEP_RECON, RK.STEP_FACES, RK.STEP_FLUXES, RK.STEP_MACRO):
+            s.step(st)
+        out.append((s.debug_get("W"), s.debug_get("WT")))
+        s.close()
+    (W, a), (_, b) = out
+    for v in range(6):
+        scale = max(np.max(np.abs(a[:, v] - W[:, v])), 1e-10 * np.max(np.abs(W[:, v])))
+        assert np.max(np.abs(a[:, v] - b[:, v])) <= 1e-5 * scale, f"variable {v}"
+
+
 def test_macro_fp32_tracks_fp64_macro_over_iterations(monkeypatch):
     """Ten iterations of the tetrahedral case in mixed precision with either macro
     solve: the moments stay within 1e-6 (relative to their largest values)."""
