@@ -22,6 +22,9 @@ constexpr int MAXF = 8;        // faces per cell
 #ifndef MICRO_PF
 #define MICRO_PF 1
 #endif
+#ifndef MICRO_FLUX_NV
+#define MICRO_FLUX_NV 4
+#endif
 #ifndef MICRO_MID_NV
 #define MICRO_MID_NV 4
 #endif
@@ -1575,7 +1578,8 @@ __global__ void k_macro_finish(Dev<T> c, int m32) {
 // per cell, faces in slot order.
 template <typename T, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_micro_flux(Dev<T> c) {
-    constexpr int NV = VW<T>::N;
+    // velocities per lane: 16-byte accesses in mixed mode
+    constexpr int NV = sizeof(T) == 8 ? 1 : MICRO_FLUX_NV;
     __shared__ int s_face[WPB][MAXF];
     __shared__ T s_n[WPB][3][MAXF], s_AV[WPB][MAXF];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
