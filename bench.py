@@ -36,8 +36,8 @@ START_ITERS = 10          # start-up iterations (first order, CFL ramp), untimed
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
 # as they stand, mixed precision, full sphere workload: one ncu capture on the same mesh
 # with every 5th velocity (K = 607), scaled by 3033/607 (traffic is proportional to K)
-NCU_TRAFFIC_MIXED = {"k_recon": 4.709e9, "k_face_interior": 5.668e9, "k_micro_sweep": 1.705e9,
-                     "k_micro_flux": 4.586e9}
+NCU_TRAFFIC_MIXED = {"k_recon": 4.731e9, "k_face_interior": 5.668e9, "k_micro_sweep": 1.706e9,
+                     "k_micro_flux": 4.563e9}
 
 
 def _peaks():

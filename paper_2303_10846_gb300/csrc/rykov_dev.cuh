@@ -22,6 +22,12 @@ constexpr int MAXF = 8;        // faces per cell
 #ifndef MICRO_PF
 #define MICRO_PF 1
 #endif
+#ifndef RECON_NV
+#define RECON_NV 4           // velocities per lane of k_recon in mixed mode (16-byte accesses)
+#endif
+#ifndef FACE_NV
+#define FACE_NV 4            // velocities per lane of k_face_interior in mixed mode (16-byte accesses)
+#endif
 #ifndef MICRO_FLUX_NV
 #define MICRO_FLUX_NV 4
 #endif
@@ -683,11 +689,12 @@ struct alignas(4 * sizeof(T)) Q4 {
     T x, y, z, w;
 };
 #ifndef RECON_MINB
-#define RECON_MINB 4         // 64 registers, four blocks of eight warps per SM
+#define RECON_MINB 3         // mixed mode: 80 registers, three blocks of eight warps per SM
+                             // (FP64: four blocks, 64 registers)
 #endif
 template <typename T, int WPB>
-__global__ void __launch_bounds__(WPB * 32, RECON_MINB) k_recon(Dev<T> c) {
-    constexpr int NV = VW<T>::N;
+__global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 4 : RECON_MINB) k_recon(Dev<T> c) {
+    constexpr int NV = sizeof(T) == 8 ? 1 : RECON_NV;
     __shared__ Q4<T> s_A[WPB][MAXF];              // LSQ weight vector, s_ij
     __shared__ Q4<T> s_B[WPB][MAXF];              // x_f - x_i, s_ij
     __shared__ Q4<T> s_C[WPB][MAXF];              // face normal
@@ -865,7 +872,7 @@ template <typename T, int WPB>
 __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c) {
     using R = Red<T>;
     using V = typename R::V;
-    constexpr int NV = VW<T>::N;
+    constexpr int NV = sizeof(T) == 8 ? 1 : FACE_NV;
     const int lane = threadIdx.x & 31;
     const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
     if (fi >= c.Fi) return;                      // whole warp: no block barriers below
