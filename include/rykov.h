@@ -101,6 +101,8 @@ int rk_version(void);
  *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4);
  *   RYKOV_PRIO=0        no stream priorities in the graph;
  *   RYKOV_PDL=0         FP32 macro phases without programmatic serialisation;
+ *   RYKOV_MACRO_LANES=L threads per cell of the FP32 macro phases, 1, 2 or 4 (default
+ *                       4; another order of the face sums, ~1e-6 of the increment);
  *   RYKOV_MACRO_FP64=1  RK_MIXED contexts run the FP64 macro PR-SGS (iterates differ
  *                       by the rounding of the FP32 solve, ~1e-6 of the increment);
  *   RYKOV_ADJ_FP64=1    RK_MIXED adjoint in FP64 (see the adjoint section). */
