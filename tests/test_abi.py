@@ -36,3 +36,19 @@ def test_params_struct_layout_matches_header():
     for _, decl in fields:
         names += [x.strip() for x in decl.split(",")]
     assert names == [f for f, _ in rykov.RkParams._fields_]
+
+
+def test_header_documents_every_environment_switch():
+    """Every RYKOV_* environment variable that the library reads is described in the
+    header next to rk_create."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_2303_10846_gb300", "csrc")
+    read = set()
+    for f in os.listdir(csrc):
+        with open(os.path.join(csrc, f)) as fh:
+            read |= set(re.findall(r'getenv\("(RYKOV_[A-Z0-9_]+)"\)', fh.read()))
+    with open(os.path.join(root, "include", "rykov.h")) as fh:
+        header = fh.read()
+    assert read, "no switches found"
+    missing = sorted(v for v in read if v not in header)
+    assert not missing, missing
