@@ -48,11 +48,18 @@ enum {
     RK_ECUDA = -3,      /* a CUDA runtime call failed                            */
     RK_EDEVICE = -4,    /* a kernel raised its device status flag                */
     RK_EDIVERGED = -5,  /* non-finite residual                                   */
-    RK_ETIMEOUT = -6,   /* reserved: bounded device wait gave up                 */
+    RK_ETIMEOUT = -6,   /* a bounded device wait gave up (cooperative solve)     */
     RK_ESTATE = -7      /* call out of order (e.g. iterate before set_state)     */
 };
 
 enum { RK_FP64 = 0, RK_MIXED = 1 };         /* context precision                 */
+/* Flags or-ed into the precision argument of rk_create:
+ *   RK_DEBUG_FLAG     reserve the verification buffers of rk_debug_get/rows;
+ *   RK_MACRO_FP32     RK_MIXED only: solve the macro PR-SGS of Step 4 in FP32 in
+ *                     delta form instead of FP64 (faster; its iterates differ from
+ *                     the FP64 solve's by ~1e-6 of the increment, and its converged
+ *                     state is the same).  FP64 contexts ignore it. */
+enum { RK_DEBUG_FLAG = 0x100, RK_MACRO_FP32 = 0x200 };
 enum { RK_WALL = 0, RK_FARFIELD = 1 };      /* boundary-condition kinds          */
 
 /* Scheme parameters.  Field order and meaning are part of the ABI. */
@@ -92,19 +99,22 @@ int rk_version(void);
  * Arithmetic: RK_FP64 computes everything in FP64.  RK_MIXED stores the
  * distributions in FP32 and computes per velocity in FP32, with compensated sums
  * over the velocities combined in FP64, FP64 moments, interface states and
- * compensation (Step 6), and the macro PR-SGS of Step 4 in FP32 in delta form: its
+ * compensation (Step 6), and the macro PR-SGS of Step 4 in FP64.  With the
+ * RK_MACRO_FP32 flag the macro PR-SGS runs in FP32 in delta form instead: its
  * constant part is formed in FP64 and every FP32 rounding is relative to the
  * increment, so the converged state is the FP64 solve's.
  * Environment switches read here (results unchanged unless noted):
  *   RYKOV_GRAPH=0       no CUDA graph of an iteration;
- *   RYKOV_COOP=1        cooperative launch of the FP64 macro PR-SGS;
+ *   RYKOV_COOP=1        cooperative launch of the FP64 macro PR-SGS (grid barriers
+ *                       between colour phases, each wait bounded by 1 s; a wait that
+ *                       runs out makes rk_implicit_iterate return RK_ETIMEOUT, once);
+ *   RYKOV_COOP_UNREACHABLE=1  tests of that bound only: the barriers wait for one
+ *                       arrival more than the grid makes, with a 50 ms bound;
  *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4);
  *   RYKOV_PRIO=0        no stream priorities in the graph;
  *   RYKOV_PDL=0         FP32 macro phases without programmatic serialisation;
  *   RYKOV_MACRO_LANES=L threads per cell of the FP32 macro phases, 1, 2 or 4 (default
  *                       4; another order of the face sums, ~1e-6 of the increment);
- *   RYKOV_MACRO_FP64=1  RK_MIXED contexts run the FP64 macro PR-SGS (iterates differ
- *                       by the rounding of the FP32 solve, ~1e-6 of the increment);
  *   RYKOV_ADJ_FP64=1    RK_MIXED adjoint in FP64 (see the adjoint section). */
 int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream);
 int rk_destroy(rk_ctx* ctx);
@@ -318,6 +328,18 @@ const char* rk_noalloc_last_error(void);
  *       J, and the total derivative dJdp[6] = dJ/dp + lam^T dR/dp.  RK_EDIVERGED if
  *       the residual becomes non-finite.
  *   rk_adjoint_get(ctx, lam, on_device): the last adjoint solution (packed). */
+/* Fused multiply-add throughput of the current device (a measurement utility with
+ * no counterpart in the paper): the ALU ceiling of the FP64 form, whose per-velocity
+ * FP64 arithmetic (GB300 issues FP64 at 1/64 of its FP32 rate) rather than HBM bounds
+ * it.  kind: RK_PEAK_FP64 (DFMA) or RK_PEAK_FP32 (FFMA).  Launches a kernel of
+ * independent FMA chains (~0.1-0.3 s) four times on `cuda_stream` (the first is a
+ * warm-up), times each with CUDA events, and returns the best rate in TFLOP/s
+ * (2 flops per FMA) in *tflops.  dev_sink: caller-owned device memory of at least 8
+ * bytes, written only to keep the chains live.  Synchronises the stream.
+ * RK_EINVAL for a bad kind or null pointer, RK_ECUDA if a launch fails. */
+enum { RK_PEAK_FP64 = 0, RK_PEAK_FP32 = 1 };
+int rk_peak_flops(int kind, uintptr_t cuda_stream, void* dev_sink, double* tflops);
+
 #define RK_NPARAM 6
 enum { RK_OBJ_HEAT = 0, RK_OBJ_DRAG = 1 };
 int rk_state_len(const rk_ctx* ctx, int64_t* n);

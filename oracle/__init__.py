@@ -83,6 +83,8 @@ def lib():
         for n in ("gradient", "faces", "fluxes", "macro", "micro"):
             getattr(L, f"orc_step_{n}").argtypes = [vp]
         L.orc_step_update.argtypes = [vp, vp]
+        L.orc_micro_point.argtypes = [vp, i64, C.c_int, i32]
+        L.orc_update_cell.argtypes = [vp, i64]
         L.orc_buffer_len.restype = i64
         L.orc_buffer_len.argtypes = [vp, C.c_int]
         L.orc_get.argtypes = [vp, C.c_int, vp]
@@ -252,6 +254,14 @@ class Oracle:
         BUF_DPHI: lambda s: (2, s.N, s.K), BUF_DT: lambda s: (s.N, 3), BUF_S: lambda s: (s.F,),
         BUF_TAUT: lambda s: (s.N,), BUF_LSTORE: lambda s: (2, s.N, s.K),
     }
+
+    def micro_point(self, cell: int, first_forward: bool = False, colour: int = 0):
+        """One point update of the micro PR-SGS for one cell (orc_micro_point)."""
+        lib().orc_micro_point(self.h, int(cell), int(bool(first_forward)), int(colour))
+
+    def update_cell(self, cell: int):
+        """Step 6 (update and compensation) for one cell (orc_update_cell)."""
+        lib().orc_update_cell(self.h, int(cell))
 
     def get(self, which: int) -> np.ndarray:
         n = lib().orc_buffer_len(self.h, which)

@@ -876,14 +876,11 @@ void orc_step_micro(orc_ctx* c) {
 /* ------------------------------------------------------------------------------ */
 /* Step 6: update and integral error compensation, Eqs. solve_rho - solve_qrot    */
 /* ------------------------------------------------------------------------------ */
-void orc_step_update(orc_ctx* c, double res_out[6]) {
-    const int64_t N = c->N, K = c->K;
+static void update_cell(orc_ctx* c, int64_t i) {
+    const int64_t K = c->K;
     const orc_params* P = &c->p;
     const double Z = P->Z_rot;
-    double* Wold = (double*)malloc(sizeof(double) * 6 * (size_t)N);
-    memcpy(Wold, c->W, sizeof(double) * 6 * (size_t)N);
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < N; ++i) {
+    {
         orc_state s;
         state_from_W(P, c->Wt + 6 * i, c->q + 6 * i, &s);
         double S[12] = {0};
@@ -929,6 +926,20 @@ void orc_step_update(orc_ctx* c, double res_out[6]) {
             q[3 + d] = S[9 + d] + qrot_t * arot;
         }
     }
+}
+
+void orc_update_cell(orc_ctx* c, int64_t cell) { update_cell(c, cell); }
+
+void orc_micro_point(orc_ctx* c, int64_t cell, int first_forward, int32_t colour) {
+    micro_point_update(c, cell, first_forward, colour);
+}
+
+void orc_step_update(orc_ctx* c, double res_out[6]) {
+    const int64_t N = c->N;
+    double* Wold = (double*)malloc(sizeof(double) * 6 * (size_t)N);
+    memcpy(Wold, c->W, sizeof(double) * 6 * (size_t)N);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) update_cell(c, i);
     /* residual: global average relative change of each macroscopic variable
      * (Sec. 4.1 names "the global average residual of macroscopic variables";
      * reading: sum_i |W^{n+1} - W^n| / sum_i |W^n| per component, the three

@@ -86,6 +86,13 @@ void     orc_step_fluxes(orc_ctx* c);     /* Step 2 (e) and Step 3              
 void     orc_step_macro(orc_ctx* c);      /* Step 4                                */
 void     orc_step_micro(orc_ctx* c);      /* Step 5                                */
 void     orc_step_update(orc_ctx* c, double res_out[6]);   /* Step 6 + residual    */
+/* The units of Steps 5 and 6 for one cell, on the context's current buffers:
+ * one point update of the micro PR-SGS (Eq. implicit_mic_final_equ: Delta phi_i from
+ * Res_i, the neighbours' Delta phi, tau~_i and the implicit step of the current
+ * iteration), and the update phi += Delta phi with the compensated W, q of Eqs.
+ * solve_rho - solve_qrot from W~_i and q_i (no residual). */
+void     orc_micro_point(orc_ctx* c, int64_t cell, int first_forward, int32_t colour);
+void     orc_update_cell(orc_ctx* c, int64_t cell);
 
 /* ---- read-back -----------------------------------------------------------------*/
 enum {

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librykov.so")
-SOURCES = ["kern_f64.cu", "kern_f32.cu", "api.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["kern_f64.cu", "kern_f32.cu", "api.cu", "noalloc.cu", "adjoint.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

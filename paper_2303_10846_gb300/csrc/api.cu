@@ -36,9 +36,9 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     // middle, last sweep); the results are the same either way
     if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::atoi(v) & 7;
     if (const char* v = std::getenv("RYKOV_PRIO")) ctx->use_prio = std::strcmp(v, "0") != 0;
-    // RYKOV_MACRO_FP64=1: mixed contexts solve the macro PR-SGS in FP64 (as FP64
-    // contexts do) instead of the FP32 delta form
-    if (const char* v = std::getenv("RYKOV_MACRO_FP64")) ctx->use_macro32 = std::strcmp(v, "1") != 0;
+    // RK_MACRO_FP32 flag: mixed contexts solve the macro PR-SGS in FP32 in delta form
+    // instead of FP64 (FP64 contexts ignore it)
+    ctx->use_macro32 = (precision & RK_MACRO_FP32) != 0;
     // RYKOV_PDL=0: the FP32 macro phases as plain launches (same results)
     if (const char* v = std::getenv("RYKOV_PDL")) ctx->use_pdl = std::strcmp(v, "0") != 0;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -410,6 +410,13 @@ static int bind_impl(rk_ctx* ctx, rk::Dev<T>& d) {
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         const int per = std::min(2, rk::Launch<T>::coop_blocks_per_sm());
         ctx->sched.coop_grid = (coop && per > 0 && ctx->use_coop) ? sms * per : 0;
+        // RYKOV_COOP_UNREACHABLE=1 (tests of the bounded wait only): the barriers of the
+        // cooperative solve wait for one arrival more than the grid makes, bounded by
+        // 50 ms, so the solve returns RK_ETIMEOUT
+        const char* ur = std::getenv("RYKOV_COOP_UNREACHABLE");
+        const bool unreachable = ur && std::strcmp(ur, "1") == 0;
+        ctx->sched.coop_extra = unreachable ? 1u : 0u;
+        ctx->sched.coop_limit_ns = unreachable ? 50000000ull : 1000000000ull;
     }
     {
         // staged micro sweeps where their shared memory fits (same results either way)
@@ -652,7 +659,12 @@ static int read_residual(rk_ctx* ctx, rk::Dev<T>& d) {
     for (int m = 0; m < 6; ++m) ctx->last_res[m] = ctx->pin[m];
     int status = 0;
     std::memcpy(&status, ctx->pin + 8, sizeof(int));
-    if (status & 4) return fail(ctx, RK_ETIMEOUT, "macro PR-SGS: a grid barrier wait gave up");
+    if (status & 4) {
+        // reported once: the flag is cleared so that the context stays usable
+        CK(cudaMemsetAsync(d.status, 0, sizeof(int), ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, RK_ETIMEOUT, "macro PR-SGS: a grid barrier wait gave up");
+    }
     return RK_OK;
 }
 

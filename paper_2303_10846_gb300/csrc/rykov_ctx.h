@@ -15,7 +15,6 @@ struct AdjState;     // adjoint workspace and solver state (adjoint.cu)
 namespace rkh {
 
 constexpr int MAX_BC = 64;
-constexpr int RK_DEBUG_FLAG = 0x100;   // precision flag: reserve verification buffers
 
 struct Carver {
     char* base;
@@ -33,7 +32,6 @@ struct Carver {
 
 using rkh::Carver;
 using rkh::MAX_BC;
-using rkh::RK_DEBUG_FLAG;
 
 #ifndef RK_STAGED_DEFAULT
 #define RK_STAGED_DEFAULT 4
@@ -85,7 +83,7 @@ struct rk_ctx {
     bool use_coop = false;            // cooperative launch of the macro PR-SGS (RYKOV_COOP=1)
     int use_staged = RK_STAGED_DEFAULT;   // staged micro sweeps, bit mask (RYKOV_STAGED)
     bool use_prio = true;                 // stream priorities for the graph branches (RYKOV_PRIO)
-    bool use_macro32 = true;              // FP32 delta-form macro PR-SGS in mixed contexts
+    bool use_macro32 = false;             // FP32 delta-form macro PR-SGS in mixed contexts
     bool use_pdl = true;                  // its phases with programmatic serialisation (RYKOV_PDL)
     cudaStream_t cap = nullptr, cap2 = nullptr;   // capture streams (main, side branch)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bnd = nullptr, ev_int = nullptr;

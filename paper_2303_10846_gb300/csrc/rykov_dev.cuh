@@ -1353,20 +1353,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier of a cooperative launch (all blocks co-resident): a counter that
 // only grows within one macro solve (k_macro_prep zeroes it); barrier number nb is
-// passed when it reaches (nb + 1) blocks x grid.  The wait is bounded: thread 0 reads
-// the clock every 1024 polls and after one second without the barrier opening records
-// status bit 4 and stops waiting, so a failure returns RK_ETIMEOUT to the host instead
-// of hanging the GPU (every other block then gives up at its own next wait).
+// passed when it reaches (nb + 1) blocks x grid (+ extra: a count that no block
+// reaches, used by a test to make the wait run out).  The wait is bounded: thread 0
+// reads the clock every 1024 polls and after limit_ns without the barrier opening
+// records status bit 4 and stops waiting, so a failure returns RK_ETIMEOUT to the host
+// instead of hanging the GPU (every other block gives up as soon as it sees the bit).
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned int* p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int& nb) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int& nb,
+                                             unsigned int extra, unsigned long long limit_ns) {
     __shared__ int s_fail;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int target = (nb + 1u) * gridDim.x;
+        const unsigned int target = (nb + 1u) * gridDim.x + extra;
         int fail = 0;
         __threadfence();
         atomicAdd(bar, 1u);
@@ -1376,7 +1378,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
             if ((++polls & 1023u) == 0u) {
                 const unsigned long long t = global_ns();
                 if (t0 == 0) t0 = t;
-                else if (t - t0 > 1000000000ull || (*(volatile int*)status & 4)) {
+                else if (t - t0 > limit_ns || (*(volatile int*)status & 4)) {
                     atomicOr(status, 4);
                     fail = 1;
                     break;
@@ -1393,7 +1395,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cell, const int* col_off,
-                                                    int C, int n_macro, unsigned int* bar) {
+                                                    int C, int n_macro, unsigned int* bar,
+                                                    unsigned int extra, unsigned long long limit_ns) {
     const int stride = (gridDim.x * blockDim.x) / MACRO_LANES;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
     const int g = (int)(threadIdx.x % MACRO_LANES);
@@ -1405,7 +1408,7 @@ __global__ void __launch_bounds__(128) k_macro_coop(Dev<T> c, const int* col_cel
                 const int lo = col_off[col], hi = col_off[col + 1];
                 const int ff = (it == 0 && dir == 0);
                 for (int t = lo + gid; t < hi; t += stride) macro_point(c, t, col_cell[t], col, ff, g);
-                if (!grid_barrier(bar, c.status, nb)) return;
+                if (!grid_barrier(bar, c.status, nb, extra, limit_ns)) return;
             }
         }
     }

@@ -37,6 +37,8 @@ struct Sched {
     const int* col_cell;            // device: cells grouped by colour
     std::vector<int> col_off;       // host: colour offsets (C+1)
     int coop_grid = 0;              // blocks of the cooperative macro solve (0: per-colour launches)
+    unsigned coop_extra = 0;        // test only: barrier arrivals that never come
+    unsigned long long coop_limit_ns = 1000000000ull;   // bound of every barrier wait
     int maxs = 0;                   // most faces of one cell
     int staged = 0;                 // micro sweeps with staged (asynchronous) row loads:
                                     // bit 0 first sweep, bit 1 middle sweeps, bit 2 last

@@ -140,7 +140,8 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_macro_coop<T>, d, sc.col_cell, d.col_off_d, C, n_macro, d.bar);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_macro_coop<T>, d, sc.col_cell, d.col_off_d, C, n_macro, d.bar,
+                                           sc.coop_extra, sc.coop_limit_ns);
         if (e == cudaSuccess) {
             pf.launches += 1;
             done = true;

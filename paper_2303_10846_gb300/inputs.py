@@ -750,11 +750,15 @@ def capsule_workload(h_wall: float = 0.047, growth: float = 1.12, h_max: float =
 
 def cone_scale_workload(h_wall: float = 0.065, growth: float = 1.12, h_max: float = 0.45,
                         dvs_target: int = 8000, ma: float = 8.0, kn: float = 0.005,
-                        T_w: float = 1.0, Z_rot: float = 3.5, cfl_imp: float = 100.0,
+                        T_w: float = 1.0, Z_rot: float = 3.5, cfl_imp: float = 20.0,
+                        first_order_iters: int = 20, cfl_ramp: float = 1.2,
                         mesh_seed: int = 20265, dvs_seed: int = 20266) -> Workload:
     """Scale case: sphere-cone (nose radius 1, 15-degree half angle, length 4, flat
     base) at zero incidence, Mach 8, Kn on the nose radius, T_w = T_inf (the case gives
-    none), in the box [-4, 10] x [-5, 5]^2: ~500k tetrahedra x ~8,000 velocities."""
+    none), in the box [-4, 10] x [-5, 5]^2: ~500k tetrahedra x ~8,000 velocities.
+    Start-up: 20 first-order iterations and an implicit CFL ramped by 1.2 per iteration
+    up to 20 (with the limited second-order scheme switched on at an implicit CFL of
+    30 or more, this case turned non-finite within 10 iterations)."""
     prof = sphere_cone_profile()
     mesh, dist = tet_axisym_body(prof, 0.0, [-4.0, -5.0, -5.0], [10.0, 5.0, 5.0], h_wall, growth,
                                  h_max, mesh_seed, "tet_cone")
@@ -763,7 +767,7 @@ def cone_scale_workload(h_wall: float = 0.065, growth: float = 1.12, h_max: floa
     dvs = unstructured_dvs(U, 1.0, T_w, ma, transitional=(kn >= 0.1), target=dvs_target,
                            seed=dvs_seed)
     params = Params(Z_rot=Z_rot, mu_ref=mu_ref_from_kn(kn, 0.74, length=1.0), cfl_imp=cfl_imp,
-                    cfl_imp0=2.0, cfl_ramp=1.3, first_order_iters=10)
+                    cfl_imp0=2.0, cfl_ramp=cfl_ramp, first_order_iters=first_order_iters)
     bcs = [BC(BC_WALL, 1.0, (0.0, 0.0, 0.0), T_w), BC(BC_FARFIELD, 1.0, U, 1.0)]
     prim = uniform_prim(mesh.n_cell, 1.0, U, 1.0)
     prim[:, 1:4] *= np.clip(dist / 1.0, 0.0, 1.0)[:, None]

@@ -18,6 +18,7 @@ RK_OK, RK_EINVAL, RK_ENOMEM, RK_ECUDA, RK_EDEVICE, RK_EDIVERGED, RK_ETIMEOUT, RK
     0, -1, -2, -3, -4, -5, -6, -7
 RK_FP64, RK_MIXED = 0, 1
 RK_DEBUG = 0x100
+RK_MACRO_FP32 = 0x200
 RK_WALL, RK_FARFIELD = 0, 1
 STEP_RECON, STEP_FACES, STEP_FLUXES, STEP_MACRO, STEP_MICRO = range(5)
 BUF = dict(PHI=0, W=1, Q=2, FACE=4, FSTATE=6, MICRO_F=7, MACRO_F=8, WT=9, RES=10, DPHI=11,
@@ -31,7 +32,8 @@ EXPORTS = ["rk_version", "rk_create", "rk_destroy", "rk_last_error", "rk_upload_
            "rk_debug_get", "rk_profile", "rk_profile_get", "rk_residual_noalloc", "rk_aero",
            "rk_noalloc_last_error", "rk_state_len", "rk_adjoint_workspace_size",
            "rk_bind_adjoint_workspace", "rk_get_state", "rk_put_state", "rk_steady_residual",
-           "rk_vjp", "rk_objective", "rk_adjoint_solve", "rk_adjoint_get", "rk_debug_rows"]
+           "rk_vjp", "rk_objective", "rk_adjoint_solve", "rk_adjoint_get", "rk_debug_rows",
+           "rk_peak_flops"]
 RK_OBJ_HEAT, RK_OBJ_DRAG = 0, 1
 OBJECTIVES = {"heat": RK_OBJ_HEAT, "drag": RK_OBJ_DRAG}
 PROF_CLASSES = ["recon", "face_interior", "face_boundary", "fluxes", "macro_sgs",
@@ -98,6 +100,7 @@ def load(path: str | None = None):
         "rk_adjoint_solve": ([vp, C.c_int, i32, dp, P(i32), vp, vp, vp], C.c_int),
         "rk_adjoint_get": ([vp, vp, C.c_int], C.c_int),
         "rk_debug_rows": ([vp, C.c_int, vp, i64, vp], C.c_int),
+        "rk_peak_flops": ([C.c_int, C.c_size_t, vp, P(dp)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -150,14 +153,27 @@ def rk_residual_noalloc(W_new, W_old, n_cell: int, res_out, stream: int) -> int:
                                       int(stream))
 
 
+def peak_tflops(kind: str = "fp64", stream=None) -> float:
+    """FMA throughput of the current device in TFLOP/s (rk_peak_flops), "fp64" or "fp32"."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = C.c_double()
+    rc = load().rk_peak_flops(0 if kind == "fp64" else 1, st.cuda_stream, _ptr(sink), C.byref(out))
+    if rc != RK_OK:
+        raise RykovError(rc, "rk_peak_flops failed")
+    return float(out.value)
+
+
 class Solver:
     """One solver context on the current CUDA device and stream.
 
     wl: a workload (mesh, dvs, params, bcs, prim0) from ``inputs``;
-    precision: "fp64" or "mixed"."""
+    precision: "fp64" or "mixed"; macro32: mixed contexts solve the macro PR-SGS in
+    FP32 delta form (RK_MACRO_FP32) instead of FP64."""
 
     def __init__(self, wl, precision: str = "fp64", stream=None, debug: bool = False,
-                 params=None):
+                 params=None, macro32: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("librykov needs a CUDA device (no CPU path exists)")
@@ -166,7 +182,8 @@ class Solver:
         self.wl = wl
         self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        prec = (RK_FP64 if precision == "fp64" else RK_MIXED) | (RK_DEBUG if debug else 0)
+        prec = ((RK_FP64 if precision == "fp64" else RK_MIXED) | (RK_DEBUG if debug else 0)
+                | (RK_MACRO_FP32 if macro32 else 0))
         self.h = rk_create(prec, self.stream.cuda_stream)
         m, d = wl.mesh, wl.dvs
         self._mesh = [_c(m.face_cell, np.int64), _c(m.face_normal, np.float64),

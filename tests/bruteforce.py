@@ -7,7 +7,7 @@ vectorised, cells are visited one at a time, the least-squares gradient uses
 the cells sorted by (colour, index) with the coefficients written with sign() exactly
 as in Eq. implicit_mic_final_equ, and Venkatakrishnan's limiter is written in its
 original (1/Delta_2)[...] form.  Agreement with the oracle to round-off pins the
-oracle's transcription (test_oracle_bruteforce.py).  Readings of the paper where it
+oracle's transcription (tests/test_oracle_solver.py).  Readings of the paper where it
 is silent are the same as the oracle's (they are part of the method definition).
 """
 from __future__ import annotations

@@ -15,6 +15,7 @@ import pytest
 
 import oracle as O
 from paper_2303_10846_gb300 import inputs as I
+from tests import patch as PT
 
 pytestmark = pytest.mark.gpu
 
@@ -24,19 +25,112 @@ def sphere():
     return I.sphere_workload()
 
 
-def _solver(wl, prec, debug=False):
+def _solver(wl, prec, debug=False, macro32=False):
     from paper_2303_10846_gb300.rykov import Solver
-    return Solver(wl, prec, debug=debug)
+    return Solver(wl, prec, debug=debug, macro32=macro32)
 
 
 TOLS = {"fp64": 1e-10, "mixed": 2e-5}
 
 
-def check_sampled(s, wl, prec, n_iter, debug, n_faces=48, n_cells=48, seed=2024):
+def _rows_of(s, name, rows):
+    rows = np.asarray(rows, np.int64)
+    return s.debug_rows(name, rows)
+
+
+def check_recon_patches(s, wl, prec, faces, phi_rows, W, q):
+    """Reconstructed face values phi(x_ij - u s_ij) (Eq. flux_solve_phi_phi: gradient,
+    limiter, upwind choice) of sampled interior faces against the oracle run on a
+    two-ring patch around the face's cells, fed the GPU's own phi rows (widened to
+    FP64 in mixed precision).  In mixed precision the upwind choice is taken on the
+    FP32 value of u.n: velocities with |u.n| < 1e-5 |u| are left out there."""
+    K = wl.dvs.K
+    u = wl.dvs.u
+    tol = TOLS[prec]
+    phi0_gpu = _rows_of(s, "FACE", faces)
+    for t, f in enumerate(faces):
+        a, b = wl.mesh.face_cell[f]
+        pw, g2l, fidx = PT.patch_workload(wl, [a, b], 2)
+        P = np.array(sorted(g2l, key=g2l.get))
+        phi = np.stack([phi_rows[int(g)] for g in P], axis=1)          # [2, n, K]
+        op = O.Oracle(pw)
+        op.set_state(W[P], q[P], phi.reshape(-1))
+        op.step("gradient")
+        op.step("faces")
+        ref = op.get(O.BUF_FACE0).reshape(2, pw.mesh.n_face, K)[:, PT.local_face(fidx, f)]
+        op.close()
+        keep = np.ones(K, bool)
+        if prec == "mixed":
+            un = u @ wl.mesh.face_normal[f]
+            keep = np.abs(un) > 1e-5 * np.linalg.norm(u, axis=1)
+        for fd in range(2):
+            sc = np.max(np.abs(phi[fd]))
+            err = np.max(np.abs(phi0_gpu[fd, t, keep] - ref[fd, keep]))
+            assert err <= tol * sc, f"face {f} field {fd}: {err / sc:.3e}"
+
+
+def check_last_sweep_patches(s, wl, prec, cells, phi_n, q_n, Wt, taut, cfl):
+    """The last point update of the micro PR-SGS (Eq. implicit_mic_final_equ) and the
+    Step-6 update (Eqs. solve_rho - solve_qrot) of sampled cells of colour 0 (the last
+    colour of the last, backward, sweep, so the neighbours' final increments are the
+    ones it read) against the oracle on a one-ring patch fed the GPU's own Res,
+    neighbour increments, W~, tau~, q^n and phi^n."""
+    m = wl.mesh
+    K = wl.dvs.K
+    tol = TOLS[prec]
+    csr = PT.cell_faces(m)
+    nb = {int(i): PT.neighbours(m, csr, int(i)) for i in cells}
+    rows = sorted(set(int(i) for i in cells) | set(j for v in nb.values() for j in v))
+    res = dict(zip(rows, np.moveaxis(_rows_of(s, "RES", rows), 1, 0)))
+    dphi = dict(zip(rows, np.moveaxis(_rows_of(s, "DPHI", rows), 1, 0)))
+    phi1 = dict(zip(cells, np.moveaxis(_rows_of(s, "PHI", cells), 1, 0)))
+    W1, q1 = s.debug_get("W"), s.debug_get("Q")
+    u, w = wl.dvs.u, wl.dvs.w
+    for i in cells:
+        i = int(i)
+        pw, g2l, _ = PT.patch_workload(wl, [i], 1, cfl_imp=cfl)
+        P = np.array(sorted(g2l, key=g2l.get))
+        n, li = len(P), g2l[i]
+        z = np.zeros((2, K))
+        op = O.Oracle(pw)
+        op.set_state(W1[P], q_n[P], np.stack([phi_n[i] if g == i else z for g in P], 1).reshape(-1))
+        op.put(O.BUF_RES, np.stack([res.get(int(g), z) for g in P], 1).reshape(-1))
+        op.put(O.BUF_DPHI, np.stack([dphi.get(int(g), z) if g != i else z for g in P], 1).reshape(-1))
+        op.put(O.BUF_WT, Wt[P].reshape(-1))
+        op.put(O.BUF_TAUT, taut[P])
+        op.micro_point(li, False, 0)
+        d_o = op.get(O.BUF_DPHI).reshape(2, n, K)[:, li]
+        sc_d = max(np.max(np.abs(dphi[j])) for j in [i] + nb[i])
+        assert np.max(np.abs(dphi[i] - d_o)) <= tol * sc_d, f"cell {i} increment"
+        op.update_cell(li)
+        p_o = op.get(O.BUF_PHI).reshape(2, n, K)[:, li]
+        assert np.max(np.abs(phi1[i] - p_o)) <= tol * np.max(np.abs(phi_n[i])), f"cell {i} phi"
+        W_o = op.get(O.BUF_W).reshape(n, 6)[li]
+        q_o = op.get(O.BUF_Q).reshape(n, 6)[li]
+        op.close()
+        # scales of the Step-6 sums: |W~| per row (momentum rows: rho |U~| + the thermal
+        # speed rho sqrt(R T~)), and for q the summed magnitudes w |c|^3 |g| of the
+        # velocity sum (a cancelling sum near equilibrium)
+        rho = Wt[i, 0]
+        R = wl.params.R
+        Tsc = Wt[i, 4] / (2.5 * rho * R)
+        msc = np.linalg.norm(Wt[i, 1:4]) + rho * np.sqrt(R * Tsc)
+        scW = np.array([rho, msc, msc, msc, abs(Wt[i, 4]), abs(Wt[i, 5])])
+        assert np.all(np.abs(W1[i] - W_o) <= tol * scW), f"cell {i} W"
+        cvec = u - Wt[i, 1:4] / rho
+        c2 = np.sum(cvec ** 2, axis=1)
+        qsc = max(0.5 * np.sum(w * c2 ** 1.5 * np.abs(phi1[i][0])), np.sum(w * np.sqrt(c2) * np.abs(phi1[i][1])))
+        assert np.max(np.abs(q1[i] - q_o)) <= tol * qsc, f"cell {i} q"
+
+
+def check_sampled(s, wl, prec, n_iter, debug, n_faces=48, n_cells=48, seed=2024,
+                  n_recon=6, n_last=6):
     """Iterate n_iter times (graph path), then step through one more iteration and
-    check sampled interior faces (interface kernel from the GPU's own phi(x_f - u s))
-    and sampled cells (micro flux by its definition from the face values, first-sweep
-    residual with the oracle's equilibrium at (W~, q^n))."""
+    check sampled interior faces (the reconstruction against the oracle on a patch;
+    the interface kernel from the GPU's own phi(x_f - u s)), sampled cells (micro flux
+    by its definition from the face values, first-sweep residual with the oracle's
+    equilibrium at (W~, q^n)) and sampled colour-0 cells (last micro point update and
+    Step-6 update against the oracle on a patch)."""
     from paper_2303_10846_gb300 import rykov as RK
     m = wl.mesh
     tol = TOLS[prec]
@@ -45,7 +139,13 @@ def check_sampled(s, wl, prec, n_iter, debug, n_faces=48, n_cells=48, seed=2024)
     interior = np.nonzero(m.face_cell[:, 1] >= 0)[0]
     faces = np.sort(rng.choice(interior, n_faces, replace=False))
     cells = np.sort(rng.choice(m.n_cell, n_cells, replace=False))
+    rfaces = faces[:n_recon]
+    csr = PT.cell_faces(m)
+    rcells = sorted(set(int(g) for f in rfaces for g in PT.grow(m, csr, m.face_cell[f], 2)))
+    phi_r = dict(zip(rcells, np.moveaxis(_rows_of(s, "PHI", rcells), 1, 0)))
+    W0, q0 = s.debug_get("W"), s.debug_get("Q")
     s.step(RK.STEP_RECON)
+    check_recon_patches(s, wl, prec, rfaces, phi_r, W0, q0)
     phi0 = s.debug_rows("FACE", faces)
     s.step(RK.STEP_FACES)
     phif = s.debug_rows("FACE", faces)
@@ -86,7 +186,12 @@ def check_sampled(s, wl, prec, n_iter, debug, n_faces=48, n_cells=48, seed=2024)
     s.step(RK.STEP_MACRO)
     Wt = s.debug_get("WT")
     taut = s.debug_get("TAUT")
+    lcells = np.sort(rng.choice(np.nonzero(m.cell_colour == 0)[0], n_last, replace=False))
+    phi_n = dict(zip(lcells, np.moveaxis(_rows_of(s, "PHI", lcells), 1, 0)))
+    dt = s.debug_get("DT")
+    cfl = dt[lcells[0], 1] / dt[lcells[0], 0]
     s.step(RK.STEP_MICRO)
+    check_last_sweep_patches(s, wl, prec, lcells, phi_n, q_n, Wt, taut, cfl)
     res = s.debug_rows("RES", cells)
     R = wl.params.R
     for j, i in enumerate(cells):
@@ -164,7 +269,6 @@ def test_cooperative_macro_solve_is_bitwise_identical_at_full_size(sphere, monke
     """The cooperative macro PR-SGS (grid barriers between colour phases) gives the same
     iterates as the per-colour launches on the full sphere (mixed context with the FP64
     macro solve, the one that has a cooperative form)."""
-    monkeypatch.setenv("RYKOV_MACRO_FP64", "1")
     a = _solver(sphere, "mixed")
     a.iterate(15)
     Wa, qa, _ = a.moments()
@@ -181,7 +285,7 @@ def test_macro_phase_launch_overlap_is_bitwise_identical_at_full_size(sphere, mo
     out = []
     for flag in ("0", "1"):
         monkeypatch.setenv("RYKOV_PDL", flag)
-        s = _solver(sphere, "mixed")
+        s = _solver(sphere, "mixed", macro32=True)
         s.iterate(15)
         out.append(s.moments()[:2])
         s.close()
@@ -219,15 +323,14 @@ def test_sphere_mixed_converges_to_1e_6(sphere):
     assert rc == 0 and np.max(res) < 1e-6 and n < 300
 
 
-def test_macro_fp32_converges_like_the_fp64_macro_solve(sphere, monkeypatch):
+def test_macro_fp32_converges_like_the_fp64_macro_solve(sphere):
     """The FP32 delta-form macro solve of mixed contexts against the FP64 one, both from
     the initial field to the residual 1e-6: the same number of iterations within 3, and
     the converged wall pressure, heat flux and C_D within 1e-5 (relative to their
     largest values)."""
     out = []
-    for flag in ("1", "0"):
-        monkeypatch.setenv("RYKOV_MACRO_FP64", flag)
-        s = _solver(sphere, "mixed")
+    for m32 in (False, True):
+        s = _solver(sphere, "mixed", macro32=m32)
         rc, n, res = s.iterate(300, tol=1e-6)
         assert rc == 0 and np.max(res) < 1e-6
         out.append((n, s.surface()[0], s.aero()))
