@@ -461,10 +461,11 @@ def sphere_extras(args, dev, peak, peak_kind):
     return out
 
 
-# FP64 operations per (cell, velocity) per iteration of the FP64 form (2 x DFMA + DADD +
-# DMUL, from ncu instruction counters on the sphere mesh with a velocity subsample,
-# divided by N*K); None until measured
-FP64_FLOPS_PER_CELL_VELOCITY = None
+# FP64 operations per (cell, velocity) per iteration of the FP64 form: 2 x DFMA + DADD +
+# DMUL summed over the per-velocity kernels (reconstruction, faces, micro flux, the 16
+# micro sweeps, cell update) by ncu's instruction counters on the sphere mesh with every
+# 10th velocity (K = 304), divided by N*K (the macro solve, O(N), is left out)
+FP64_FLOPS_PER_CELL_VELOCITY = 1152.6
 
 
 def run_gpu(args, rank, world, local_rank):

@@ -113,6 +113,8 @@ int rk_version(void);
  *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4);
  *   RYKOV_PRIO=0        no stream priorities in the graph;
  *   RYKOV_PDL=0         FP32 macro phases without programmatic serialisation;
+ *   RYKOV_PACKED=0      RK_MIXED per-velocity kernels with scalar FP32 arithmetic
+ *                       instead of packed FP32 pairs (rounding-level differences);
  *   RYKOV_MACRO_LANES=L threads per cell of the FP32 macro phases, 1, 2 or 4 (default
  *                       4; another order of the face sums, ~1e-6 of the increment);
  *   RYKOV_ADJ_FP64=1    RK_MIXED adjoint in FP64 (see the adjoint section). */

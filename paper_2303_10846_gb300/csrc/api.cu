@@ -41,6 +41,9 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     ctx->use_macro32 = (precision & RK_MACRO_FP32) != 0;
     // RYKOV_PDL=0: the FP32 macro phases as plain launches (same results)
     if (const char* v = std::getenv("RYKOV_PDL")) ctx->use_pdl = std::strcmp(v, "0") != 0;
+    // RYKOV_PACKED=0: the mixed-precision kernels with scalar FP32 arithmetic instead of
+    // the packed pairs (same steps, rounding-level differences)
+    if (const char* v = std::getenv("RYKOV_PACKED")) ctx->use_packed = std::strcmp(v, "0") != 0;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     for (int b = 0; b < MAX_BC; ++b) ctx->bck[b] = -1;
     std::memset(ctx->bcv, 0, sizeof(ctx->bcv));
@@ -279,6 +282,7 @@ static size_t carve(rk_ctx* ctx, char* base, rk::Dev<T>& d) {
     d.fnT = cv.take<T>(3 * F); d.fsT = cv.take<T>(F);
     d.iterp = cv.take<double>(4);
     d.debug = ctx->debug ? 1 : 0;
+    d.packed = ctx->use_packed ? 1 : 0;
     d.face_int = cv.take<int>(ctx->Fi + 1); d.face_bnd = cv.take<int>(ctx->Fb + 1);
     d.bcv = cv.take<double>(MAX_BC * 5); d.bck = cv.take<int>(MAX_BC);
     d.u = cv.take<double>(3 * Kp); d.w = cv.take<double>(Kp);

@@ -70,6 +70,7 @@ constexpr double PI = 3.14159265358979323846;
 struct DevBase {
     int N, F, K, Kp, C, Fi, Fb, nnz;
     int debug;                         // write verification-only records (face states)
+    int packed;                        // mixed mode: kernels on the packed FP32 pipe
     // implicit-step schedule, evaluated on the device each iteration (k_iter_begin)
     double cfl_imp, cfl_imp0, cfl_ramp;
     int first_order_iters, limiter, limiter_freeze;

@@ -1,6 +1,7 @@
 // Definitions of the launch sequences (included by kern_f64.cu / kern_f32.cu only).
 #pragma once
 
+#include "rykov_dev_packed.cuh"
 #include "rykov_launch.cuh"
 
 namespace rk {
@@ -32,7 +33,14 @@ template <typename T>
 cudaError_t Launch<T>::recon(const Dev<T>& d, cudaStream_t s, Prof& pf) {
     k_iter_begin<T><<<1, 1, 0, s>>>(d);
     pf.begin(0, s);
-    k_recon<T, RECON_WPB><<<cdiv(d.N, RECON_WPB), RECON_WPB * 32, 0, s>>>(d);
+    if constexpr (std::is_same<T, float>::value) {
+        if (d.packed)
+            k_recon_p<RECON_WPB><<<cdiv(d.N, RECON_WPB), RECON_WPB * 32, 0, s>>>(d);
+        else
+            k_recon<T, RECON_WPB><<<cdiv(d.N, RECON_WPB), RECON_WPB * 32, 0, s>>>(d);
+    } else {
+        k_recon<T, RECON_WPB><<<cdiv(d.N, RECON_WPB), RECON_WPB * 32, 0, s>>>(d);
+    }
     pf.end(s);
     pf.launches += 2;
     return cudaGetLastError();
@@ -192,7 +200,29 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             pf.begin(sw == 0 ? 5 : (sw == nsw - 1 ? 7 : 6), s);
             const int* cl = sc.col_cell + lo;
             const int kind = sw == 0 ? 0 : (sw == nsw - 1 ? 2 : 1);
-            if ((sc.staged >> kind) & 1) {
+            bool done = false;
+            if constexpr (std::is_same<T, float>::value) {
+                if (d.packed && ((sc.staged >> kind) & 1)) {
+                    constexpr int W = MICRO_ST_WPB;
+                    const dim3 g(cdiv(n, W)), b(W * 32);
+                    const int mx = sc.maxs;
+                    if (sw == 0)
+                        k_micro_sweep_st_p<W, true, false><<<g, b, StBytes<T>::template get<true, false>(mx), s>>>(d, cl, n, col, mx);
+                    else if (sw == nsw - 1)
+                        k_micro_sweep_st_p<W, false, true><<<g, b, StBytes<T>::template get<false, true>(mx), s>>>(d, cl, n, col, mx);
+                    else
+                        k_micro_sweep_st_p<W, false, false><<<g, b, StBytes<T>::template get<false, false>(mx), s>>>(d, cl, n, col, mx);
+                    done = true;
+                } else if (d.packed) {
+                    const dim3 g(cdiv(n, MICRO_WPB)), b(MICRO_WPB * 32);
+                    if (sw == 0) k_micro_sweep_p<MICRO_WPB, true, false><<<g, b, 0, s>>>(d, cl, n, col);
+                    else if (sw == nsw - 1) k_micro_sweep_p<MICRO_WPB, false, true><<<g, b, 0, s>>>(d, cl, n, col);
+                    else k_micro_sweep_p<MICRO_WPB, false, false><<<g, b, 0, s>>>(d, cl, n, col);
+                    done = true;
+                }
+            }
+            if (done) {
+            } else if ((sc.staged >> kind) & 1) {
                 constexpr int W = MICRO_ST_WPB;
                 const dim3 g(cdiv(n, W)), b(W * 32);
                 const int mx = sc.maxs;
@@ -238,6 +268,15 @@ size_t Launch<T>::micro_staged_smem(int maxs) {
         cudaFuncSetAttribute(k_micro_sweep_st<T, W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)StBytes<T>::template get<false, false>(maxs)) != cudaSuccess)
         return 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (cudaFuncSetAttribute(k_micro_sweep_st_p<W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)StBytes<T>::template get<true, false>(maxs)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)StBytes<T>::template get<false, true>(maxs)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)StBytes<T>::template get<false, false>(maxs)) != cudaSuccess)
+            return 0;
+    }
     return need2;
 }
 
