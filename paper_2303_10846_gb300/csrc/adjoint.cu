@@ -27,6 +27,10 @@ struct AdjState {
     double *vzero = nullptr, *jv = nullptr, *lam = nullptr, *rv = nullptr, *tmp = nullptr,
            *tmp2 = nullptr, *V = nullptr;
     double* stage = nullptr;       // packed staging for host inputs / outputs
+    // macroscopic part of the preconditioner: a padded phi-block temporary, the
+    // (W, q) outputs of the collision-coupling product, the macro adjoint iterate and
+    // the inverse macro diagonals
+    double *pc1 = nullptr, *pcW = nullptr, *mY = nullptr, *mDinv = nullptr;
     // mixed-precision contexts: FP64 copies of phi and of the frozen limiter values,
     // s_ij per slot (the FP64 view of the context's FP32 per-velocity arrays)
     double *phi64 = nullptr, *lstore64 = nullptr, *slot_s64 = nullptr;
@@ -81,6 +85,10 @@ static size_t adj_carve(rk_ctx* ctx, int m, char* base, AdjState& A) {
     A.tmp2 = cv.take<double>(A.np);
     A.V = cv.take<double>((size_t)(m + 1) * A.np);
     A.stage = cv.take<double>(A.n);
+    A.pc1 = cv.take<double>(2 * N * Kp);
+    A.pcW = cv.take<double>(12 * N);
+    A.mY = cv.take<double>(6 * N);
+    A.mDinv = cv.take<double>(2 * N);
     A.slot_s64 = cv.take<double>(nnz);
     if (ctx->prec == RK_MIXED) {
         A.phi64 = cv.take<double>(2 * N * Kp);
@@ -337,6 +345,85 @@ static cudaError_t adj_precond(rk_ctx* ctx, AdjState& A, const double* in, doubl
     return cudaGetLastError();
 }
 
+// out = P^-T in with the macroscopic coupling of the forward iteration (transposed):
+//   t     = S^-T (in_phi + M_Y^T in_Y)              transposed micro sweeps
+//   x     = L^-T (B_W^T t)                          transposed macro PR-SGS sweeps
+//   out   = -(t + M_W^T x),  -in_Y                  (the sign convention of adj_precond)
+static cudaError_t adj_precond_macro(rk_ctx* ctx, AdjState& A, const double* in, double* out) {
+    cudaStream_t s = ctx->stream;
+    const size_t N = ctx->N, n1 = 2 * N * (size_t)ctx->Kp;
+    const rk::Dev<double> d = dview(ctx, A);
+    const double* zW = A.vzero + n1;               // zero (W, q) blocks
+    rk::k_adj_momT<<<1216, 256, 0, s>>>(d, in, in + n1, in + n1 + 6 * N, 1.0, A.pc1);
+    cudaError_t e = cudaMemsetAsync(out, 0, n1 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    rk::AdjBufs a = adj_bufs(ctx, A, in, out);
+    const int C = ctx->C;
+    const bool f32 = adj_fp32(ctx);
+    for (int sw = 0; sw < ctx->p.n_micro_sgs; ++sw) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int cc = 0; cc < C; ++cc) {
+                const int col = dir == 0 ? cc : C - 1 - cc;
+                const int lo = ctx->col_off[col], n = ctx->col_off[col + 1] - lo;
+                if (n == 0) continue;
+                if (f32)
+                    rk::k_adj_sweep<rk::ADJ_WPB, float><<<rk::cdv(n, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(
+                        d, a, ctx->sched.col_cell + lo, n, A.pc1, out);
+                else
+                    rk::k_adj_sweep<rk::ADJ_WPB, double><<<rk::cdv(n, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(
+                        d, a, ctx->sched.col_cell + lo, n, A.pc1, out);
+                A.launches++;
+            }
+        }
+    }
+    // B_W^T t: the collision coupling's W derivative applied to t (k_adj_cell, mode 2,
+    // with zero (W, q) weights)
+    rk::AdjBufs b = adj_bufs(ctx, A, out, nullptr);
+    b.vW = zW;
+    b.vq = zW + 6 * N;
+    b.oW = A.pcW;
+    b.oq = A.pcW + 6 * N;
+    const int gc = rk::cdv(ctx->N, rk::ADJ_WPB);
+    if (f32) {
+        float* vf = reinterpret_cast<float*>(A.nbg) + 8 * (size_t)ctx->N * ctx->Kp;
+        rk::k_adj_downcast<<<1216, 256, 0, s>>>(out, vf, n1);
+        b.vphif = vf;
+        rk::k_adj_cell<rk::ADJ_WPB, float><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, b, 2);
+        A.launches += 2;
+    } else {
+        rk::k_adj_cell<rk::ADJ_WPB, double><<<gc, rk::ADJ_WPB * 32, 0, s>>>(d, b, 2);
+        A.launches++;
+    }
+    // L^-T (B_W^T t) by transposed colour sweeps of the macro operator
+    rk::k_adj_macro_prep<<<rk::cdv(ctx->N, 128), 128, 0, s>>>(d, A.tau, A.mDinv);
+    if ((e = cudaMemsetAsync(A.mY, 0, 6 * N * sizeof(double), s)) != cudaSuccess) return e;
+    for (int it = 0; it < ctx->p.n_macro_sgs; ++it) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int cc = 0; cc < C; ++cc) {
+                const int col = dir == 0 ? cc : C - 1 - cc;
+                const int lo = ctx->col_off[col], n = ctx->col_off[col + 1] - lo;
+                if (n == 0) continue;
+                rk::k_adj_macro_sweepT<<<rk::cdv(n, 128), 128, 0, s>>>(d, ctx->sched.col_cell + lo, n, A.mDinv,
+                                                                      A.pcW, A.mY);
+                A.launches++;
+            }
+        }
+    }
+    // t + M_W^T x, then the signs
+    rk::k_adj_momT<<<1216, 256, 0, s>>>(d, out, A.mY, zW, 1.0, out);
+    rk::k_adj_precond_finish<<<1216, 256, 0, s>>>(in, out, n1, A.np);
+    A.launches += 4;
+    return cudaGetLastError();
+}
+
+// the preconditioner of the adjoint solve: the transposed micro sweeps alone (default),
+// or with the macroscopic coupling (RYKOV_ADJ_PC=macro)
+static cudaError_t adj_pc(rk_ctx* ctx, AdjState& A, const double* in, double* out) {
+    const char* v = std::getenv("RYKOV_ADJ_PC");
+    if (v && std::strcmp(v, "macro") == 0) return adj_precond_macro(ctx, A, in, out);
+    return adj_precond(ctx, A, in, out);
+}
+
 // dots of x with V_0..V_{m-1} into dev (device), deterministic
 static void adj_mdot(rk_ctx* ctx, AdjState& A, const double* x, const double* V, int m, double* dev) {
     rk::k_vec_mdot<<<rk::VEC_GRID, rk::VEC_BS, 0, ctx->stream>>>(x, V, A.np, m, A.np, A.part);
@@ -553,7 +640,7 @@ extern "C" int rk_adjoint_solve(rk_ctx* ctx, int objective, int32_t max_iter, do
         for (int j = 0; j < m && total < max_iter; ++j) {
             double* Vj = A.V + (size_t)j * A.np;
             double* w = A.V + (size_t)(j + 1) * A.np;
-            CK(adj_precond(ctx, A, Vj, A.tmp));
+            CK(adj_pc(ctx, A, Vj, A.tmp));
             CK(adj_apply(ctx, A, A.tmp, w, 0.0, 0));
             // two passes of classical Gram-Schmidt
             adj_mdot(ctx, A, w, A.V, j + 1, A.hd);
@@ -595,7 +682,7 @@ extern "C" int rk_adjoint_solve(rk_ctx* ctx, int objective, int32_t max_iter, do
         CK(cudaMemsetAsync(A.tmp2, 0, A.np * sizeof(double), s));
         rk::k_vec_madd<<<1216, 256, 0, s>>>(A.tmp2, A.V, A.np, jj, A.hd, A.np);
         A.launches++;
-        CK(adj_precond(ctx, A, A.tmp2, A.tmp));
+        CK(adj_pc(ctx, A, A.tmp2, A.tmp));
         vec_axpby(ctx, A, 1.0, A.tmp, 1.0, A.lam);
         if ((rc = residual(&beta))) return rc;
     }

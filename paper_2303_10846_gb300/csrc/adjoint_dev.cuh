@@ -997,4 +997,108 @@ __global__ void k_vec_madd(double* y, const double* V, size_t ld, int m, const d
     }
 }
 
+
+// ------------------------------------------------------------------------------------
+// Macroscopic part of the adjoint preconditioner.  The forward iteration (Sec. 3.5)
+// predicts W~ from the moments of the micro residual by the implicit macroscopic
+// system (Eq. implicit_mac_equ_fin) before the micro sweeps use phi*(W~); linearised
+// at a steady state it maps a residual r to
+//   dW~ = L^-1 M_W r_phi,  dphi = S^-1 (r_phi + B_W dW~),  dY = M_Y dphi + r_Y,
+// L the macro operator, S the micro PR-SGS operator, M_W / M_Y the moment rows of R_W /
+// (R_W, R_q), B_W = dR_phi/dW.  Its transpose, applied by these kernels with the
+// transposed micro sweeps, is the adjoint's preconditioner.
+// ------------------------------------------------------------------------------------
+// out = base + sgn * M_Y^T (yW, yq) per (cell, velocity): the weights of phi in the rows
+// R_W (moments 1, u, |u|^2/2 of g; h in the energy rows) and R_q (c|c|^2/2 of g, c of h,
+// c = u - U(W)); base may be null (zero).
+__global__ void k_adj_momT(Dev<double> c, const double* base, const double* yW, const double* yq,
+                           double sgn, double* out) {
+    const size_t NK = (size_t)c.N * c.Kp;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NK; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = t / c.Kp;
+        const int k = (int)(t - i * c.Kp);
+        double og = 0.0, oh = 0.0;
+        if (k < c.K) {
+            const double* W = c.W + 6 * i;
+            const double rho = W[0], U[3] = {W[1] / rho, W[2] / rho, W[3] / rho};
+            const double ux = c.u[k], uy = c.u[c.Kp + k], uz = c.u[2 * c.Kp + k], w = c.w[k];
+            const double* a = yW + 6 * i;
+            const double* b = yq + 6 * i;
+            const double cx = ux - U[0], cy = uy - U[1], cz = uz - U[2];
+            const double c2 = cx * cx + cy * cy + cz * cz;
+            og = w * (a[0] + ux * a[1] + uy * a[2] + uz * a[3] + 0.5 * (ux * ux + uy * uy + uz * uz) * a[4] +
+                      0.5 * c2 * (cx * b[0] + cy * b[1] + cz * b[2]));
+            oh = w * (a[4] + a[5] + cx * b[3] + cy * b[4] + cz * b[5]);
+        }
+        out[t] = (base ? base[t] : 0.0) + sgn * og;
+        out[NK + t] = (base ? base[NK + t] : 0.0) + sgn * oh;
+    }
+}
+
+// Per cell: 1/D and 1/(D + 1/(Z tau)) of the macro operator, D = 1/(cfl dt) +
+// sum_f (A_f / 2V) r_f (the forward macro solve's diagonal, Eq. implicit_mac_equ_fin)
+__global__ void k_adj_macro_prep(Dev<double> c, const double* tau, double* dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
+    double D = 1.0 / (c.cfl_imp * c.dt[i]);
+    const double iv = 1.0 / c.vol[i];
+    for (int m = c.slot_off[i]; m < c.slot_off[i + 1]; ++m) {
+        const int f = c.slot_face[m];
+        D += 0.5 * c.fa[f] * iv * c.rf[f];
+    }
+    dinv[2 * (size_t)i] = 1.0 / D;
+    dinv[2 * (size_t)i + 1] = 1.0 / (D + 1.0 / (c.Z * tau[i]));
+}
+
+// J(W; n)^T y: the transposed Jacobian of the Euler flux G(W).n (Eq.
+// implicit_mac_equ_euler_flux; p = (2/5)(rho E - rho |U|^2 / 2), rotational energy
+// convected) applied to y, i.e. the gradient of y . G(W; n) in W
+__device__ __forceinline__ void euler_jt(const double* W, double nx, double ny, double nz, const double* y,
+                                         double* o) {
+    const double rho = W[0], ir = 1.0 / rho;
+    const double U[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
+    const double Un = U[0] * nx + U[1] * ny + U[2] * nz;
+    const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+    const double p = 0.4 * (W[4] - 0.5 * rho * U2);
+    const double s = y[1] * W[1] + y[2] * W[2] + y[3] * W[3];
+    const double yn = y[1] * nx + y[2] * ny + y[3] * nz;
+    const double EpUn = (W[4] + p) * ir;          // (E + p) / rho
+    o[0] = -s * Un * ir + yn * 0.2 * U2 + y[4] * (0.2 * U2 * Un - EpUn * Un) - y[5] * W[5] * Un * ir;
+    const double n[3] = {nx, ny, nz};
+    for (int k = 0; k < 3; ++k)
+        o[1 + k] = y[0] * n[k] + y[1 + k] * Un + s * n[k] * ir - 0.4 * yn * U[k] +
+                   y[4] * (-0.4 * U[k] * Un + EpUn * n[k]) + y[5] * W[5] * n[k] * ir;
+    o[4] = 0.4 * yn + 1.4 * y[4] * Un;
+    o[5] = y[5] * Un;
+}
+
+// One colour phase of a point Gauss-Seidel sweep on the transposed macro operator L^T:
+// for every cell j of the colour, y_j = D_j^-1 (b_j - sum_i c_ij (J(W_j; n_ij)^T y_i -
+// r_ij y_i)) over the interior neighbours i, c_ij = A_f / (2 V_i), n_ij the normal out
+// of i (the forward operator's coefficient of dW_j in cell i's row, transposed).
+__global__ void __launch_bounds__(128) k_adj_macro_sweepT(Dev<double> c, const int* cells, int n,
+                                                          const double* dinv, const double* b, double* y) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int j = cells[t];
+    const double* Wj = c.W + 6 * (size_t)j;
+    double acc[6];
+    for (int q = 0; q < 6; ++q) acc[q] = b[6 * (size_t)j + q];
+    for (int m = c.slot_off[j]; m < c.slot_off[j + 1]; ++m) {
+        const int i = c.slot_nbr[m];
+        if (i < 0) continue;
+        const int f = c.slot_face[m];
+        // the normal out of j is sg n_f; out of i it is -sg n_f
+        const double sg = c.slot_left[m] ? -1.0 : 1.0;
+        const double cij = 0.5 * c.fa[f] / c.vol[i];
+        double yi[6], jt[6];
+        for (int q = 0; q < 6; ++q) yi[q] = y[6 * (size_t)i + q];
+        euler_jt(Wj, sg * c.fn[f], sg * c.fn[c.F + f], sg * c.fn[2 * c.F + f], yi, jt);
+        for (int q = 0; q < 6; ++q) acc[q] -= cij * (jt[q] - c.rf[f] * yi[q]);
+    }
+    const double d0 = dinv[2 * (size_t)j], d1 = dinv[2 * (size_t)j + 1];
+    for (int q = 0; q < 5; ++q) y[6 * (size_t)j + q] = acc[q] * d0;
+    y[6 * (size_t)j + 5] = acc[5] * d1;
+}
+
 }  // namespace rk
