@@ -321,14 +321,13 @@ const char* rk_noalloc_last_error(void);
  *       with respect to X (packed, may be NULL) and its explicit p-derivative dJdp[6].
  *   rk_adjoint_solve(ctx, objective, max_iter, tol, iters_done, rel_res, J, dJdp):
  *       solves (dR/dX)^T lam = -dJ/dX by restarted GMRES, right-preconditioned with
- *       the transposed point Gauss-Seidel sweeps of the micro PR-SGS operator
- *       (n_micro_sgs x forward + backward colour sweeps; implicit CFL cfl_imp) on the
- *       phi block and -1 on the (W, q) block, or (environment variable
- *       RYKOV_ADJ_PC=macro) with the transpose of the forward iteration's linearised
- *       step: those sweeps coupled through the collision term's W derivative to
- *       n_macro_sgs transposed colour sweeps of the macro operator of Eq.
- *       implicit_mac_equ_fin and back through the moments; stops when
- *       ||(dR/dX)^T lam + dJ/dX||_2 <=
+ *       the transpose of the forward iteration's linearised step: the transposed
+ *       point Gauss-Seidel sweeps of the micro PR-SGS operator (n_micro_sgs x forward
+ *       + backward colour sweeps; implicit CFL cfl_imp), coupled through the collision
+ *       term's W derivative to n_macro_sgs transposed colour sweeps of the macro
+ *       operator of Eq. implicit_mac_equ_fin and back through the moments (the
+ *       environment variable RYKOV_ADJ_PC=micro keeps the micro sweeps alone, with -1
+ *       on the (W, q) block); stops when ||(dR/dX)^T lam + dJ/dX||_2 <=
  *       tol ||dJ/dX||_2 or after max_iter Krylov iterations, starting from the last
  *       solution of the same objective at the same state (0 otherwise).  Returns the
  *       iterations done, the final relative residual (recomputed, not estimated),

@@ -416,12 +416,12 @@ static cudaError_t adj_precond_macro(rk_ctx* ctx, AdjState& A, const double* in,
     return cudaGetLastError();
 }
 
-// the preconditioner of the adjoint solve: the transposed micro sweeps alone (default),
-// or with the macroscopic coupling (RYKOV_ADJ_PC=macro)
+// the preconditioner of the adjoint solve: with the macroscopic coupling (default), or
+// the transposed micro sweeps alone (RYKOV_ADJ_PC=micro)
 static cudaError_t adj_pc(rk_ctx* ctx, AdjState& A, const double* in, double* out) {
     const char* v = std::getenv("RYKOV_ADJ_PC");
-    if (v && std::strcmp(v, "macro") == 0) return adj_precond_macro(ctx, A, in, out);
-    return adj_precond(ctx, A, in, out);
+    if (v && std::strcmp(v, "micro") == 0) return adj_precond(ctx, A, in, out);
+    return adj_precond_macro(ctx, A, in, out);
 }
 
 // dots of x with V_0..V_{m-1} into dev (device), deterministic
