@@ -112,7 +112,7 @@ int rk_version(void);
  *                       arrival more than the grid makes, with a 50 ms bound;
  *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4);
  *   RYKOV_PRIO=0        no stream priorities in the graph;
- *   RYKOV_PDL=0         FP32 macro phases without programmatic serialisation;
+ *   RYKOV_PDL=0         macro phases without programmatic serialisation;
  *   RYKOV_PACKED=0      RK_MIXED per-velocity kernels with scalar FP32 arithmetic
  *                       instead of packed FP32 pairs (rounding-level differences);
  *   RYKOV_MACRO_LANES=L threads per cell of the FP32 macro phases, 1, 2 or 4 (default
@@ -266,11 +266,14 @@ int rk_profile_get(rk_ctx* ctx, double* ms, int64_t* counts);
  * work overlaps on that GPU (for instance on two streams) race on it and give wrong
  * results; calls on different devices do not, each device having its own copy.
  * Each call overwrites every part of the array it reads, so nothing carries over
- * from one call to the next.  The first call on a device (with that
- * device current) looks the array's device address up once; make that first call
- * before any stream capture.  Returns RK_OK, RK_EINVAL (null pointer, bad size) or
- * RK_ECUDA; rk_noalloc_last_error() gives the message of the last failed call on
- * the calling thread.  Asynchronous: the result is ready when the stream reaches it. */
+ * from one call to the next.  Every call made outside stream capture looks the
+ * array's device address up on the current device (so the address stays valid after
+ * a device reset); a call during capture reuses the address of the last uncaptured
+ * call on that device, so make one call on each device before any stream capture.
+ * Returns RK_OK, RK_EINVAL (null pointer, bad size) or RK_ECUDA;
+ * rk_noalloc_last_error() gives the message of the calling thread's last call (empty
+ * after a call that succeeded).  Asynchronous: the result is ready when the stream
+ * reaches it. */
 #define RK_NOALLOC_MAX_CELLS 1048576
 int rk_residual_noalloc(const double* W_new, const double* W_old, int64_t n_cell,
                         double* res_out, uintptr_t cuda_stream);

@@ -540,7 +540,7 @@ extern "C" int rk_steady_residual(rk_ctx* ctx, double* r, int on_device) {
     d.debug = 0;
     cudaStream_t s = ctx->stream;
     rk::k_recon<double, 8><<<rk::cdv(ctx->N, 8), 256, 0, s>>>(d);
-    if (ctx->Fi) rk::k_face_interior<double, 8><<<rk::cdv(ctx->Fi, 8), 256, 0, s>>>(d);
+    if (ctx->Fi) rk::k_face_interior<double, 8, 1><<<rk::cdv(ctx->Fi, 8), 256, 0, s>>>(d);
     if (ctx->Fb) rk::k_face_boundary<double, 256><<<ctx->Fb, 256, 0, s>>>(d);
     rk::AdjBufs a = adj_bufs(ctx, A, A.vzero, A.tmp);
     rk::k_adj_residual<rk::ADJ_WPB><<<rk::cdv(ctx->N, rk::ADJ_WPB), rk::ADJ_WPB * 32, 0, s>>>(d, a);

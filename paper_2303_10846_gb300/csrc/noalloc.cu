@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(NA_BS) k_res_final(const double* part, int nbl
 
 extern "C" int rk_residual_noalloc(const double* W_new, const double* W_old, int64_t n_cell,
                                    double* res_out, uintptr_t cuda_stream) {
+    g_err.clear();                   // the message describes this call only
     if (!W_new || !W_old || !res_out) return na_fail(RK_EINVAL, "rk_residual_noalloc: null pointer");
     if (n_cell <= 0) return na_fail(RK_EINVAL, "rk_residual_noalloc: n_cell must be positive");
     if (n_cell > RK_NOALLOC_MAX_CELLS)
@@ -94,10 +95,18 @@ extern "C" int rk_residual_noalloc(const double* W_new, const double* W_old, int
     if (e != cudaSuccess) return na_fail(RK_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(RK_EINVAL, "rk_residual_noalloc: device id out of range");
     double* part = nullptr;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     {
-        // first call on this device (which is current): look up the array's device
-        // address; the symbol name itself is only a host-side stand-in
+        // look up the array's device address on this device (which is current): the
+        // symbol name itself is only a host-side stand-in.  It is looked up again on
+        // every call outside stream capture (so a device reset, which reloads the
+        // module, cannot leave a stale address); during capture the address of the
+        // last uncaptured call on this device is used
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) return na_fail(RK_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
         std::lock_guard<std::mutex> lk(g_mu);
+        if (cs == cudaStreamCaptureStatusNone) g_addr[dev] = nullptr;
         if (!g_addr[dev]) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_partials);
@@ -108,7 +117,6 @@ extern "C" int rk_residual_noalloc(const double* W_new, const double* W_old, int
         part = g_addr[dev];
     }
     const int nblocks = (int)((n_cell + NA_BS - 1) / NA_BS);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     k_res_partials<<<nblocks, NA_BS, 0, s>>>(W_new, W_old, (int)n_cell, part);
     k_res_final<<<1, NA_BS, 0, s>>>(part, nblocks, res_out);
     e = cudaGetLastError();

@@ -28,6 +28,9 @@ constexpr int MAXF = 8;        // faces per cell
 #ifndef FACE_NV
 #define FACE_NV 4            // velocities per lane of k_face_interior in mixed mode (16-byte accesses)
 #endif
+#ifndef FACE_FW
+#define FACE_FW 4            // warps per interior face in mixed mode (k_face_interior)
+#endif
 #ifndef MICRO_FLUX_NV
 #define MICRO_FLUX_NV 4
 #endif
@@ -869,22 +872,31 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 4 : RECON_MINB) k_r
 #ifndef FACE_MINB
 #define FACE_MINB 3          // 80 registers, three blocks of eight warps per SM
 #endif
-template <typename T, int WPB>
+// FW warps share one face (each takes every FW-th chunk of 32 x NV velocities; their
+// partial sums are combined in a fixed order through shared memory), so that fewer
+// faces are in flight and pass 2 finds the face rows of pass 1 still in L2.
+template <typename T, int WPB, int FW>
 __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c) {
     using R = Red<T>;
     using V = typename R::V;
     constexpr int NV = sizeof(T) == 8 ? 1 : FACE_NV;
-    const int lane = threadIdx.x & 31;
-    const int fi = blockIdx.x * WPB + (threadIdx.x >> 5);
-    if (fi >= c.Fi) return;                      // whole warp: no block barriers below
-    const int f = c.face_int[fi];
+    constexpr int FPB = WPB / FW;                // faces per block
+    constexpr int NB = EQN + 2;
+    __shared__ V s_v[FW > 1 ? FPB : 1][FW][17];
+    __shared__ T s_cst[FW > 1 ? FPB : 1][NB];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int fib = wib / FW, sub = wib % FW;
+    const int fi = blockIdx.x * FPB + fib;
+    if (FW == 1 && fi >= c.Fi) return;           // whole warp: no block barriers below
+    const bool active = fi < c.Fi;               // (FW > 1: every warp meets the barriers)
+    const int f = active ? c.face_int[fi] : c.face_int[0];
     const size_t FK = (size_t)c.F * c.Kp;
     T* g0 = c.face + (size_t)f * c.Kp;
     T* h0 = c.face + FK + (size_t)f * c.Kp;
     // reference velocity U_r (any value is exact; the mean of the cells' U^n keeps
     // the shifted moments small)
     T Ur[3] = {T(0), T(0), T(0)};
-    if (lane == 0) {
+    if (lane == 0 && active) {
         const int a = c.fc[2 * f], b = c.fc[2 * f + 1];
         const double* Wa = c.W + 6 * (size_t)a;
         const double* Wb = c.W + 6 * (size_t)b;
@@ -904,7 +916,7 @@ __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c)
         T p2[12];
 #pragma unroll
         for (int j = 0; j < 12; ++j) p2[j] = T(0);
-        for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+        for (int k0 = NV * (lane + 32 * sub); active && k0 < c.K; k0 += 32 * NV * FW) {
             T ux[NV], uy[NV], uz[NV], wv[NV], gv[NV], hv[NV], t[5];
             vload(c.uT + k0, ux);
             vload(c.uT + c.Kp + k0, uy);
@@ -938,13 +950,23 @@ __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c)
         }
     }
     warp_red_lane0<T, 17>(v);
+    if constexpr (FW > 1) {
+        if (lane == 0)
+            for (int j = 0; j < 17; ++j) s_v[fib][sub][j] = v[j];
+        __syncthreads();
+        if (lane == 0 && sub == 0)
+            for (int j = 0; j < 17; ++j) {
+                V t = s_v[fib][0][j];
+                for (int q = 1; q < FW; ++q) t = R::add(t, s_v[fib][q][j]);
+                v[j] = t;
+            }
+    }
     // interface state on lane 0, in the per-velocity arithmetic type T (the moments
     // themselves are carried with compensation)
-    constexpr int NB = EQN + 2;
     T cst[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) cst[j] = T(0);
-    if (lane == 0) {
+    if (lane == 0 && sub == 0 && active) {
         T x[17];
         for (int j = 0; j < 17; ++j) x[j] = (T)R::to_T(v[j]);
         const T Rg = par<T>(c, 0), Z = par<T>(c, 1), s = c.fsT[f];
@@ -987,14 +1009,22 @@ __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c)
         }
     }
     T e[NB];
+    if constexpr (FW > 1) {
+        if (lane == 0 && sub == 0)
+            for (int j = 0; j < NB; ++j) s_cst[fib][j] = cst[j];
+        __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NB; ++j) e[j] = __shfl_sync(0xffffffffu, cst[j], 0);
+        for (int j = 0; j < NB; ++j) e[j] = s_cst[fib][j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) e[j] = __shfl_sync(0xffffffffu, cst[j], 0);
+    }
     const T nx = c.fnT[f], ny = c.fnT[c.F + f], nz = c.fnT[2 * c.F + f];
     const T a = e[0], b = e[1];
     V r6[6];
     {
         Acc<T> m[6];
-        for (int k0 = NV * lane; k0 < c.K; k0 += 32 * NV) {
+        for (int k0 = NV * (lane + 32 * sub); active && k0 < c.K; k0 += 32 * NV * FW) {
             T ux[NV], uy[NV], uz[NV], wv[NV], gv[NV], hv[NV], t[6];
             vload(c.uT + k0, ux);
             vload(c.uT + c.Kp + k0, uy);
@@ -1029,8 +1059,21 @@ __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c)
         for (int j = 0; j < 6; ++j) r6[j] = R::from(m[j]);
     }
     warp_red_lane0<T, 6>(r6);
-    if (lane == 0)
-        for (int d = 0; d < 6; ++d) R::store(c.mface + (size_t)f * 6 + d, r6[d]);
+    if constexpr (FW > 1) {
+        if (lane == 0)
+            for (int j = 0; j < 6; ++j) s_v[fib][sub][j] = r6[j];
+        __syncthreads();
+        if (lane == 0 && sub == 0 && active) {
+            for (int d = 0; d < 6; ++d) {
+                V t = s_v[fib][0][d];
+                for (int q = 1; q < FW; ++q) t = R::add(t, s_v[fib][q][d]);
+                R::store(c.mface + (size_t)f * 6 + d, t);
+            }
+        }
+    } else {
+        if (lane == 0)
+            for (int d = 0; d < 6; ++d) R::store(c.mface + (size_t)f * 6 + d, r6[d]);
+    }
 }
 
 // Boundary faces (reading; the paper names diffuse reflection but gives no formula):
@@ -1260,6 +1303,16 @@ __global__ void k_macro_prep(Dev<T> c) {
     for (int q = 0; q < 6; ++q) c.dW[6 * (size_t)i + q] = 0.0;
 }
 
+// Launched with programmatic stream serialisation: each phase waits for the previous
+// one to complete, its writes visible, before it reads anything (griddepcontrol.wait),
+// and only then lets the next one be launched (griddepcontrol.launch_dependents), so
+// that the launch latency of the next colour overlaps this one while at most one phase
+// waits ahead.  Both are no-ops in a plain launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // One point update of the macro PR-SGS (Eq. implicit_mac_equ_fin) for every cell of
 // one colour, one thread per cell:
 //   dW~_i = [Res_i - sum_j (A/2V) ((G(W_j + dW~_j) - G(W_j)) - r dW~_j)] / D_i,
@@ -1341,6 +1394,9 @@ __device__ __forceinline__ void macro_point(const Dev<T>& c, int p, int i, int c
 template <typename T>
 __global__ void __launch_bounds__(128) k_macro_sweep(Dev<T> c, const int* col_cell, int lo, int n, int colour,
                                                      int first_forward) {
+    // phases launched with programmatic stream serialisation (see pdl_wait)
+    pdl_wait();
+    pdl_launch_dependents();
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) / MACRO_LANES;
     if (t >= n) return;                           // whole lane group
     macro_point(c, lo + t, col_cell[lo + t], colour, first_forward, (int)(threadIdx.x % MACRO_LANES));
@@ -1477,15 +1533,6 @@ __global__ void k_macro_prep32(Dev<T> c) {
     dl[0] = dl[1] = dl[2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Launched with programmatic stream serialisation: each phase waits for the previous
-// one to complete, its writes visible, before it reads anything (griddepcontrol.wait),
-// and only then lets the next one be launched (griddepcontrol.launch_dependents), so
-// that the launch latency of the next colour overlaps this one while at most one phase
-// waits ahead.  Both are no-ops in a plain launch.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // LN threads per cell, each taking every LN-th face, the partial sums combined by a
 // butterfly (every lane of the group ends with the same bits; lane 0 stores).

@@ -50,7 +50,8 @@ template <typename T>
 cudaError_t Launch<T>::faces_interior(const Dev<T>& d, cudaStream_t s, Prof& pf) {
     if (d.Fi) {
         pf.begin(1, s);
-        k_face_interior<T, FACE_WPB><<<cdiv(d.Fi, FACE_WPB), FACE_WPB * 32, 0, s>>>(d);
+        constexpr int FW = sizeof(T) == 4 ? FACE_FW : 1;
+        k_face_interior<T, FACE_WPB, FW><<<cdiv(d.Fi, FACE_WPB / FW), FACE_WPB * 32, 0, s>>>(d);
         pf.end(s);
         pf.launches += 1;
     }
@@ -157,14 +158,26 @@ cudaError_t Launch<T>::macro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
             (void)cudaGetLastError();
         }
     }
+    // per-colour phases, each overlapping the launch of the next (programmatic stream
+    // serialisation) unless sc.pdl is 0
+    cudaLaunchAttribute pattr[1];
+    pattr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pattr[0].val.programmaticStreamSerializationAllowed = 1;
     for (int it = 0; it < n_macro && !done; ++it) {
         for (int dir = 0; dir < 2; ++dir) {
             for (int cc = 0; cc < C; ++cc) {
                 const int col = dir == 0 ? cc : C - 1 - cc;
                 const int lo = sc.col_off[col], n = sc.col_off[col + 1] - lo;
                 if (!n) continue;
-                k_macro_sweep<T><<<cdiv((long long)n * MACRO_LANES, 128), 128, 0, s>>>(d, sc.col_cell, lo, n, col,
-                                                              it == 0 && dir == 0);
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)cdiv((long long)n * MACRO_LANES, 128));
+                cfg.blockDim = dim3(128);
+                cfg.stream = s;
+                cfg.attrs = pattr;
+                cfg.numAttrs = sc.pdl ? 1 : 0;
+                const cudaError_t e = cudaLaunchKernelEx(&cfg, k_macro_sweep<T>, d, (const int*)sc.col_cell, lo, n, col,
+                                                         (int)(it == 0 && dir == 0));
+                if (e != cudaSuccess) return e;
                 pf.launches += 1;
             }
         }

@@ -242,8 +242,8 @@ def test_adjoint_sphere_converges_and_matches_finite_differences(sphere_first_or
     s = Solver(wl, "fp64", params=wl.params)
     rc, n, res = s.iterate(800, tol=1e-13)
     assert rc == 0 and np.max(res) < 1e-13, (n, res)
-    base = s.get_state()
     s.bind_adjoint(20)
+    base = s.get_state()
     adj = {}
     for obj in ("heat", "drag"):
         it, rel, J, dJdp = s.adjoint_solve(obj, max_iter=200, tol=1e-10)

@@ -380,6 +380,8 @@ def test_invalid_inputs_are_rejected():
 
 @pytest.mark.parametrize("prec,env,m32", [("fp64", {"RYKOV_COOP": "1"}, False),
                                           ("fp64", {"RYKOV_GRAPH": "0"}, False),
+                                          ("fp64", {"RYKOV_PDL": "0"}, False),
+                                          ("mixed", {"RYKOV_PDL": "0"}, False),
                                           ("mixed", {"RYKOV_GRAPH": "0"}, False),
                                           ("mixed", {"RYKOV_COOP": "1"}, False),
                                           ("mixed", {"RYKOV_GRAPH": "0"}, True),
