@@ -29,7 +29,8 @@ constexpr int MAXF = 8;        // faces per cell
 #define FACE_NV 4            // velocities per lane of k_face_interior in mixed mode (16-byte accesses)
 #endif
 #ifndef FACE_FW
-#define FACE_FW 4            // warps per interior face in mixed mode (k_face_interior)
+#define FACE_FW 1            // warps per interior face in mixed mode (k_face_interior; 2, 4
+                             // and 8 measured slower: the kernel is issue-bound)
 #endif
 #ifndef MICRO_FLUX_NV
 #define MICRO_FLUX_NV 4
