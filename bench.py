@@ -163,9 +163,32 @@ def oracle_rate(wl, iters, warmup=0):
     return wl.mesh.n_cell * wl.dvs.K * iters / dt, dt
 
 
-def cpu_sample_desc(wl, w2, stride, what):
-    return (f"{what} of the full mesh (N={w2.mesh.n_cell}) with every {stride}th velocity "
-            f"(K={w2.dvs.K} of {wl.dvs.K}, weights x{stride})")
+def oracle_sample_rate(name, stride, iters, warmup, threads=None):
+    """The oracle on the bounded sample of workload `name` (every stride-th velocity)
+    in a fresh child process (no CUDA context, no torch thread pool beside OpenMP):
+    the same start-up iterations as the GPU arm (first order, CFL ramp), `warmup`
+    more, then `iters` timed iterations of the limited second-order scheme.
+    Returns (updates/s of the sample, seconds per iteration, sample K, start-up)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "wl = bench.dvs_sample(bench.workload(sys.argv[1]), int(sys.argv[2])); "
+            "start = max(bench.START_ITERS, wl.params.first_order_iters + 2); "
+            "v, dt = bench.oracle_rate(wl, int(sys.argv[3]), start + int(sys.argv[4])); "
+            "print(json.dumps({'v': v, 'dt': dt, 'K': wl.dvs.K, 'start': start}))" % ROOT)
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    r = subprocess.run([sys.executable, "-c", code, name, str(stride), str(iters), str(warmup)],
+                       capture_output=True, text=True, env=env, timeout=1800)
+    line = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not line:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-500:])
+    d = json.loads(line[-1])
+    return d["v"], d["dt"] / iters, d["K"], d["start"]
+
+
+def cpu_sample_desc(wl, sample_k, stride, what):
+    return (f"{what} of the full mesh (N={wl.mesh.n_cell}) with every {stride}th velocity "
+            f"(K={sample_k} of {wl.dvs.K}, weights x{stride}), in a child process")
 
 
 def oracle_table(steps=2):
@@ -195,19 +218,18 @@ def run_reference(args, rank, world):
         return None
     wl = workload(args.workload)
     stride = CPU_STRIDE[args.workload]
-    w2 = dvs_sample(wl, stride)
-    v, dt = oracle_rate(w2, args.steps, args.warmup)
+    v, dt, sk, start = oracle_sample_rate(args.workload, stride, args.steps, args.warmup)
     cores = _cores()
     out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": wl.name, "N": wl.mesh.n_cell, "K": wl.dvs.K,
-                      "sample_K": w2.dvs.K, "precision": "fp64", "l2": "n/a (CPU)"},
+                      "sample_K": sk, "precision": "fp64", "l2": "n/a (CPU)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": cpu_sample_desc(wl, w2, stride,
-                                                      f"{args.warmup} warm-up + {args.steps} timed "
-                                                      f"oracle iterations")},
+                            "sample": cpu_sample_desc(
+                                wl, sk, stride, f"{start} start-up + {args.warmup} warm-up + "
+                                f"{args.steps} timed oracle iterations")},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if not args.no_oracle_table:
         out["oracle_table"] = oracle_table()
@@ -461,6 +483,36 @@ def sphere_extras(args, dev, peak, peak_kind):
     return out
 
 
+def config_table(args):
+    """The other configurations beside the headline: the 8^3 cavity in FP64 (its run of
+    200 implicit iterations from rest, and the throughput of single iterations) and the
+    capsule in mixed precision (throughput over second-order iterations, then the wall
+    time to residual 1e-6 from the free-stream start, capped at --capsule-cap)."""
+    from paper_2303_10846_gb300 import inputs as I
+    noop = lambda: None
+    out = {}
+    wl = I.cavity_workload()
+    c = Case(wl, "fp64")
+    run = c.converge(200, tol=0.0)
+    c.timed(args.steps, args.warmup, max(START_ITERS, wl.params.first_order_iters + 2), noop)
+    out["cavity_fp64"] = {"workload": wl.name, "N": wl.mesh.n_cell, "K": wl.dvs.K,
+                          "ms_per_step": round(c.ms, 4),
+                          "value": wl.mesh.n_cell * wl.dvs.K / (c.ms * 1e-3),
+                          "run_200_iterations": {"wall_s": run["wall_s"],
+                                                 "final_residual": run["final_residual"]}}
+    c.close()
+    if args.capsule_cap > 0:
+        wl = I.capsule_workload()
+        c = Case(wl, "mixed")
+        c.timed(args.steps, args.warmup, max(START_ITERS, wl.params.first_order_iters + 2), noop)
+        out["capsule_mixed"] = {"workload": wl.name, "N": wl.mesh.n_cell, "K": wl.dvs.K,
+                                "ms_per_step": round(c.ms, 4),
+                                "value": wl.mesh.n_cell * wl.dvs.K / (c.ms * 1e-3),
+                                "time_to_residual": c.converge(args.capsule_cap)}
+        c.close()
+    return out
+
+
 # FP64 operations per (cell, velocity) per iteration of the FP64 form: 2 x DFMA + DADD +
 # DMUL summed over the per-velocity kernels (reconstruction, faces, micro flux, the 16
 # micro sweeps, cell update) by ncu's instruction counters on the sphere mesh with every
@@ -527,15 +579,22 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0:
         if not args.no_cpu:
             stride = CPU_STRIDE[args.workload]
-            w2 = dvs_sample(workload(args.workload) if args.kstride > 1 else wl, stride)
-            v, dt = oracle_rate(w2, 2)
+            full = workload(args.workload) if args.kstride > 1 else wl
+            # the iterations the GPU arm times: the same start-up and warm-up, then
+            # --steps timed iterations (the oracle's time per iteration falls over the
+            # first second-order iterations, so a shorter run would not compare)
+            v, dt, sk, start = oracle_sample_rate(args.workload, stride, args.steps, args.warmup)
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-                                   "sample": cpu_sample_desc(wl, w2, stride, "2 oracle iterations")}
+                                   "sample": cpu_sample_desc(
+                                       full, sk, stride, f"{start} start-up + {args.warmup} warm-up + "
+                                       f"{args.steps} timed oracle iterations")}
         else:
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
                                    "sample": "skipped"}
         if not args.no_extras and args.workload == "scale":
             out["sphere"] = sphere_extras(args, dev, peak, peak_kind)
+            if not args.no_configs:
+                out["configs"] = config_table(args)
             if conv is None:
                 out["time_to_residual"] = dict(out["sphere"].get("time_to_residual") or {},
                                                workload=out["sphere"]["workload"])
@@ -555,6 +614,10 @@ def main():
                     help="skip the sphere case (throughput, time to residual, FP64 form, adjoint)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the sphere's FP64 form")
     ap.add_argument("--no-oracle-table", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the cavity (FP64) and capsule (mixed) rows")
+    ap.add_argument("--capsule-cap", type=int, default=400,
+                    help="iteration cap of the capsule's time-to-residual-1e-6 run (0: skip the capsule)")
     ap.add_argument("--start", type=int, default=START_ITERS)
     ap.add_argument("--converge", type=int, default=600,
                     help="iteration cap of the sphere's time-to-residual-1e-6 run (0: skip)")
