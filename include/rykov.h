@@ -110,7 +110,9 @@ int rk_version(void);
  *                       runs out makes rk_implicit_iterate return RK_ETIMEOUT, once);
  *   RYKOV_COOP_UNREACHABLE=1  tests of that bound only: the barriers wait for one
  *                       arrival more than the grid makes, with a 50 ms bound;
- *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4);
+ *   RYKOV_STAGED=b      micro sweeps with staged row loads (bit mask, default 4;
+ *                       + 8: the cell's own rows by bulk copies with mbarrier
+ *                       completion in the packed kernels, same results);
  *   RYKOV_PRIO=0        no stream priorities in the graph;
  *   RYKOV_PDL=0         macro phases without programmatic serialisation;
  *   RYKOV_PACKED=0      RK_MIXED per-velocity kernels with scalar FP32 arithmetic

@@ -34,7 +34,7 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     if (const char* v = std::getenv("RYKOV_COOP")) ctx->use_coop = std::strcmp(v, "0") != 0;
     // RYKOV_STAGED: which micro sweeps stage their row loads (bits 0/1/2: first,
     // middle, last sweep); the results are the same either way
-    if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::atoi(v) & 7;
+    if (const char* v = std::getenv("RYKOV_STAGED")) ctx->use_staged = std::atoi(v) & 15;
     if (const char* v = std::getenv("RYKOV_PRIO")) ctx->use_prio = std::strcmp(v, "0") != 0;
     // RK_MACRO_FP32 flag: mixed contexts solve the macro PR-SGS in FP32 in delta form
     // instead of FP64 (FP64 contexts ignore it)

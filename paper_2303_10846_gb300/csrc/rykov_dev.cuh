@@ -28,6 +28,13 @@ constexpr int MAXF = 8;        // faces per cell
 #ifndef FACE_NV
 #define FACE_NV 4            // velocities per lane of k_face_interior in mixed mode (16-byte accesses)
 #endif
+#ifndef FACE_CG
+#define FACE_CG 1            // k_face_interior reads the face rows through L2 only
+#endif
+#ifndef FACE_PADSEL
+#define FACE_PADSEL 1        // 1: the K padding zeroed by a select per velocity (0: in a tail
+                             // branch; measured 43.9 vs 38.6 ms at scale: code generation)
+#endif
 #ifndef FACE_FW
 #define FACE_FW 1            // warps per interior face in mixed mode (k_face_interior; 2, 4
                              // and 8 measured slower: the kernel is issue-bound)
@@ -161,6 +168,16 @@ __device__ __forceinline__ float dot_split(float ax, float ay, float az, float b
 // the 1e-5 target of the mixed mode)
 __device__ __forceinline__ double ex(double x) { return exp(x); }
 __device__ __forceinline__ float ex(float x) { return __expf(x); }
+// 2^x for the equilibria (exponents pre-scaled by log2(e)): FP64 exp2 in FP64 mode;
+// in mixed mode the hardware approximation (PTX ex2.approx.f32: relative error ~2^-22,
+// subnormal results kept), one instruction where the accurate exp2f takes a longer
+// path for the very negative exponents of the high-speed tails of the DVS
+__device__ __forceinline__ double ex2(double x) { return exp2(x); }
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 // quotient of the limiter function: exact in FP64 mode
@@ -415,6 +432,18 @@ __device__ __forceinline__ void vload(const float* p, float (&x)[4]) {
 __device__ __forceinline__ void vstore(float* p, const float (&x)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
 }
+// streaming loads cached in L2 only (ld.global.cg): rows read once per pass leave the
+// L1 lines of the velocity tables in place
+__device__ __forceinline__ void vload_cg(const float* p, float (&x)[4]) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ __forceinline__ void vload_cg(const float* p, float (&x)[2]) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    x[0] = v.x; x[1] = v.y;
+}
+__device__ __forceinline__ void vload_cg(const float* p, float (&x)[1]) { x[0] = __ldcg(p); }
+__device__ __forceinline__ void vload_cg(const double* p, double (&x)[1]) { x[0] = __ldcg(p); }
 __device__ __forceinline__ void vload(const double* p, double (&x)[1]) { x[0] = *p; }
 __device__ __forceinline__ void vload(const float* p, float (&x)[1]) { x[0] = *p; }
 __device__ __forceinline__ void vstore(float* p, const float (&x)[1]) { *p = x[0]; }
@@ -422,6 +451,14 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[2]) {
     *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
 }
 __device__ __forceinline__ void vstore(double* p, const double (&x)[1]) { *p = x[0]; }
+template <typename T, int NV>
+__device__ __forceinline__ void vload_row(const T* p, T (&x)[NV]) {
+#if FACE_CG
+    vload_cg(p, x);
+#else
+    vload(p, x);
+#endif
+}
 
 // ------------------------------------------------------------------------------------
 // gas model
@@ -487,6 +524,16 @@ __device__ __forceinline__ S viscosity_T(const Dev<T>& c, S Ttr) {
     return par<S>(c, 2) * pow(Ttr / par<S>(c, 3), par<S>(c, 4));
 }
 
+// The constants of one reduced Rykov equilibrium G+ = (1 - 1/Z) G_tr + G_rot / Z,
+// H+ likewise (Eqs. eqdf_G* - eqdf_Rrot), with the weights 1 - 1/Z and 1/Z folded
+// into the Maxwellians, the heat-flux factors into the q vectors and log2(e) into the
+// exponents, so that eval_eq needs no more than one operation per factor:
+//   e[0..2] U;  e[3..5] q_tr / (15 R T_tr p_tr);  e[6..8] q_rot
+//   e[9]  (1 - 1/Z) rho (2 pi R T_tr)^-3/2;  e[10] -log2(e) / (2 R T_tr);  e[11] 1 / R T_tr
+//   e[12] omega0 (R T_tr p_tr) / (R T p)  (ratio of the two heat-flux factors)
+//   e[13] rho (2 pi R T)^-3/2 / Z;  e[14] -log2(e) / (2 R T);  e[15] 1 / R T
+//   e[16] R T_rot;  e[17] R T;  e[18] R T_rot (1 - delta) / (R T_tr p_rot);
+//   e[19] omega1 (1 - delta) / p;  e[20..22] unused (zero)
 template <typename T, typename S>
 __device__ void make_eq(const Dev<T>& c, S rho, const S* U, S Tq, S Ttr, S Trot, const S* qtr,
                         const S* qrot, S* e) {
@@ -494,39 +541,40 @@ __device__ void make_eq(const Dev<T>& c, S rho, const S* U, S Tq, S Ttr, S Trot,
             del = par<S>(c, 7);
     const S RTtr = R * Ttr, RT = R * Tq, RTrot = R * Trot;
     const S ptr = rho * RTtr, p = rho * RT, prot = rho * RTrot;
-    for (int d = 0; d < 3; ++d) { e[d] = U[d]; e[3 + d] = qtr[d]; e[6 + d] = qrot[d]; }
+    const S qf = S(1) / (S(15) * RTtr * ptr);
+    for (int d = 0; d < 3; ++d) { e[d] = U[d]; e[3 + d] = qtr[d] * qf; e[6 + d] = qrot[d]; }
+    const S l2e = S(1.4426950408889634);
     const S a = S(2.0 * PI) * RTtr;
-    e[9] = rho / (a * sqrt(a));
-    e[10] = S(1) / (S(2) * RTtr);
-    e[11] = S(1) / (S(15) * RTtr * ptr);
-    e[12] = S(1) / RTtr;
+    e[9] = (S(1) - S(1) / Z) * rho / (a * sqrt(a));
+    e[10] = -l2e / (S(2) * RTtr);
+    e[11] = S(1) / RTtr;
+    e[12] = om0 * (RTtr * ptr) / (RT * p);
     const S b = S(2.0 * PI) * RT;
-    e[13] = rho / (b * sqrt(b));
-    e[14] = S(1) / (S(2) * RT);
-    e[15] = om0 / (S(15) * RT * p);
-    e[16] = S(1) / RT;
-    e[17] = RTrot;
-    e[18] = RT;
-    e[19] = (S(1) - del) / (RTtr * prot);
-    e[20] = om1 * (S(1) - del) / (RT * p);
-    e[21] = S(1) - S(1) / Z;
-    e[22] = S(1) / Z;
+    e[13] = rho / (b * sqrt(b)) / Z;
+    e[14] = -l2e / (S(2) * RT);
+    e[15] = S(1) / RT;
+    e[16] = RTrot;
+    e[17] = RT;
+    e[18] = RTrot * (S(1) - del) / (RTtr * prot);
+    e[19] = om1 * (S(1) - del) / p;
+    e[20] = e[21] = e[22] = S(0);
 }
 
+// G+ and H+ at velocity u from make_eq's constants:
+//   G_tr = M_tr (1 + c.q_tr (c^2 / R T_tr - 5) / (15 R T_tr p_tr)), G_rot likewise at T
+//   with omega0; H = R T_rot G_tr + R T G_rot + c.q_rot (weighted Maxwellian terms)
 template <typename T>
 __device__ __forceinline__ void eval_eq(const T* e, T ux, T uy, T uz, T& G, T& H) {
-    T cx = ux - e[0], cy = uy - e[1], cz = uz - e[2];
-    T c2 = cx * cx + cy * cy + cz * cz;
-    T cqt = cx * e[3] + cy * e[4] + cz * e[5];
-    T cqr = cx * e[6] + cy * e[7] + cz * e[8];
-    T mtr = e[9] * ex(-c2 * e[10]);
-    T m = e[13] * ex(-c2 * e[14]);
-    T Gtr = mtr * (T(1) + cqt * e[11] * (c2 * e[12] - T(5)));
-    T Grot = m * (T(1) + cqt * e[15] * (c2 * e[16] - T(5)));
-    T Htr = e[17] * (Gtr + e[19] * cqr * mtr);
-    T Hrot = e[18] * (Grot + e[20] * cqr * m);
-    G = e[21] * Gtr + e[22] * Grot;
-    H = e[21] * Htr + e[22] * Hrot;
+    const T cx = ux - e[0], cy = uy - e[1], cz = uz - e[2];
+    const T c2 = cx * cx + cy * cy + cz * cz;
+    const T cqt = cx * e[3] + cy * e[4] + cz * e[5];
+    const T cqr = cx * e[6] + cy * e[7] + cz * e[8];
+    const T mtr = e[9] * ex2(c2 * e[10]);
+    const T m = e[13] * ex2(c2 * e[14]);
+    const T Gtr = mtr + mtr * (cqt * (c2 * e[11] - T(5)));
+    const T Grot = m + m * ((cqt * e[12]) * (c2 * e[15] - T(5)));
+    G = Gtr + Grot;
+    H = e[16] * Gtr + e[17] * Grot + cqr * (e[18] * mtr + e[19] * m);
 }
 
 template <typename T>
@@ -923,8 +971,8 @@ __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c)
             vload(c.uT + c.Kp + k0, uy);
             vload(c.uT + 2 * c.Kp + k0, uz);
             vload(c.wT + k0, wv);
-            vload(g0 + k0, gv);
-            vload(h0 + k0, hv);
+            vload_row(g0 + k0, gv);
+            vload_row(h0 + k0, hv);
 #pragma unroll
             for (int e = 0; e < NV; ++e) {
                 const T cx = ux[e] - Ur[0], cy = uy[e] - Ur[1], cz = uz[e] - Ur[2];
@@ -1026,30 +1074,41 @@ __global__ void __launch_bounds__(WPB * 32, FACE_MINB) k_face_interior(Dev<T> c)
     {
         Acc<T> m[6];
         for (int k0 = NV * (lane + 32 * sub); active && k0 < c.K; k0 += 32 * NV * FW) {
-            T ux[NV], uy[NV], uz[NV], wv[NV], gv[NV], hv[NV], t[6];
+            T ux[NV], uy[NV], uz[NV], wv[NV], u2[NV], gv[NV], hv[NV], t[6];
             vload(c.uT + k0, ux);
             vload(c.uT + c.Kp + k0, uy);
             vload(c.uT + 2 * c.Kp + k0, uz);
             vload(c.wT + k0, wv);
-            vload(g0 + k0, gv);
-            vload(h0 + k0, hv);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u2[q] = T(0.5) * (ux[q] * ux[q] + uy[q] * uy[q] + uz[q] * uz[q]);
+            vload_row(g0 + k0, gv);
+            vload_row(h0 + k0, hv);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 T G, H;
                 eval_eq(e + 2, ux[q], uy[q], uz[q], G, H);
-                // the K padding keeps zero face values
+#if FACE_PADSEL
                 const bool pad = k0 + q >= c.K;
                 const T gf = pad ? T(0) : a * gv[q] + b * G;
                 const T hf = pad ? T(0) : a * hv[q] + b * H;
+#else
+                const T gf = a * gv[q] + b * G;
+                const T hf = a * hv[q] + b * H;
+#endif
                 gv[q] = gf;
                 hv[q] = hf;
+                // zero weight in the K padding: no flux terms there
                 const T wu = wv[q] * (ux[q] * nx + uy[q] * ny + uz[q] * nz);
                 const T wg = wu * gf;
-                const T tv[6] = {wg, wg * ux[q], wg * uy[q], wg * uz[q],
-                                 wu * (T(0.5) * (ux[q] * ux[q] + uy[q] * uy[q] + uz[q] * uz[q]) * gf + hf),
-                                 wu * hf};
+                const T tv[6] = {wg, wg * ux[q], wg * uy[q], wg * uz[q], wu * (u2[q] * gf + hf), wu * hf};
 #pragma unroll
                 for (int j = 0; j < 6; ++j) t[j] = q == 0 ? tv[j] : t[j] + tv[j];
+            }
+            if (!FACE_PADSEL && k0 + NV > c.K) {
+                // the K padding keeps zero face values
+#pragma unroll
+                for (int q = 0; q < NV; ++q)
+                    if (k0 + q >= c.K) gv[q] = hv[q] = T(0);
             }
             vstore(g0 + k0, gv);
             vstore(h0 + k0, hv);

@@ -41,7 +41,8 @@ struct Sched {
     unsigned long long coop_limit_ns = 1000000000ull;   // bound of every barrier wait
     int maxs = 0;                   // most faces of one cell
     int staged = 0;                 // micro sweeps with staged (asynchronous) row loads:
-                                    // bit 0 first sweep, bit 1 middle sweeps, bit 2 last
+                                    // bit 0 first sweep, bit 1 middle sweeps, bit 2 last;
+                                    // bit 3: the cell's own rows by bulk copies (packed)
     int macro32 = 0;                // macro PR-SGS in FP32 delta form (mixed contexts)
     int pdl = 1;                    // its colour phases launched with programmatic
                                     // stream serialisation

@@ -219,12 +219,18 @@ cudaError_t Launch<T>::micro(const Dev<T>& d, cudaStream_t s, const Sched& sc, i
                     constexpr int W = MICRO_ST_WPB;
                     const dim3 g(cdiv(n, W)), b(W * 32);
                     const int mx = sc.maxs;
-                    if (sw == 0)
-                        k_micro_sweep_st_p<W, true, false><<<g, b, StBytes<T>::template get<true, false>(mx), s>>>(d, cl, n, col, mx);
-                    else if (sw == nsw - 1)
-                        k_micro_sweep_st_p<W, false, true><<<g, b, StBytes<T>::template get<false, true>(mx), s>>>(d, cl, n, col, mx);
-                    else
-                        k_micro_sweep_st_p<W, false, false><<<g, b, StBytes<T>::template get<false, false>(mx), s>>>(d, cl, n, col, mx);
+                    const size_t sb = sw == 0 ? StBytes<T>::template get<true, false>(mx)
+                                              : (sw == nsw - 1 ? StBytes<T>::template get<false, true>(mx)
+                                                               : StBytes<T>::template get<false, false>(mx));
+                    if ((sc.staged >> 3) & 1) {            // the cell's own rows by bulk copies
+                        if (sw == 0) k_micro_sweep_st_p<W, true, false, true><<<g, b, sb, s>>>(d, cl, n, col, mx);
+                        else if (sw == nsw - 1) k_micro_sweep_st_p<W, false, true, true><<<g, b, sb, s>>>(d, cl, n, col, mx);
+                        else k_micro_sweep_st_p<W, false, false, true><<<g, b, sb, s>>>(d, cl, n, col, mx);
+                    } else {
+                        if (sw == 0) k_micro_sweep_st_p<W, true, false, false><<<g, b, sb, s>>>(d, cl, n, col, mx);
+                        else if (sw == nsw - 1) k_micro_sweep_st_p<W, false, true, false><<<g, b, sb, s>>>(d, cl, n, col, mx);
+                        else k_micro_sweep_st_p<W, false, false, false><<<g, b, sb, s>>>(d, cl, n, col, mx);
+                    }
                     done = true;
                 } else if (d.packed) {
                     const dim3 g(cdiv(n, MICRO_WPB)), b(MICRO_WPB * 32);
@@ -282,12 +288,16 @@ size_t Launch<T>::micro_staged_smem(int maxs) {
                              (int)StBytes<T>::template get<false, false>(maxs)) != cudaSuccess)
         return 0;
     if constexpr (std::is_same<T, float>::value) {
-        if (cudaFuncSetAttribute(k_micro_sweep_st_p<W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)StBytes<T>::template get<true, false>(maxs)) != cudaSuccess ||
-            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)StBytes<T>::template get<false, true>(maxs)) != cudaSuccess ||
-            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)StBytes<T>::template get<false, false>(maxs)) != cudaSuccess)
+        const int b0 = (int)StBytes<T>::template get<true, false>(maxs);
+        const int b1 = (int)StBytes<T>::template get<false, true>(maxs);
+        const int b2 = (int)StBytes<T>::template get<false, false>(maxs);
+        constexpr auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (cudaFuncSetAttribute(k_micro_sweep_st_p<W, true, false, false>, A, b0) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, true, false>, A, b1) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, false, false>, A, b2) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, true, false, true>, A, b0) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, true, true>, A, b1) != cudaSuccess ||
+            cudaFuncSetAttribute(k_micro_sweep_st_p<W, false, false, true>, A, b2) != cudaSuccess)
             return 0;
     }
     return need2;
