@@ -42,10 +42,11 @@ START_ITERS = 10          # start-up iterations (first order, CFL ramp), untimed
 # every S-th velocity (weights x S), used by the cpu_baseline key and the reference arm
 CPU_STRIDE = {"scale": 50, "sphere": 30}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels
-# as they stand, mixed precision, from one ncu capture of the same mesh with a subsample
-# of the velocities, scaled to the full K (traffic is proportional to K); None: no
-# capture of the current kernels
-NCU_TRAFFIC = {"scale": {}, "sphere": {}}
+# as they stand, mixed precision, from one full-size ncu capture of one second-order
+# iteration of each workload (one pass; the micro sweeps: the 16 launches' total / 16);
+# a kernel changed since the capture has no entry
+NCU_TRAFFIC = {"scale": {"k_micro_sweep": 36.20e9, "k_recon": 111.03e9, "k_face_interior": 189.69e9},
+               "sphere": {"k_micro_sweep": 1.694e9, "k_recon": 4.978e9, "k_face_interior": 6.791e9}}
 
 
 def _peaks():
