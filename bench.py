@@ -518,7 +518,7 @@ def config_table(args):
 # DMUL summed over the per-velocity kernels (reconstruction, faces, micro flux, the 16
 # micro sweeps, cell update) by ncu's instruction counters on the sphere mesh with every
 # 10th velocity (K = 304), divided by N*K (the macro solve, O(N), is left out)
-FP64_FLOPS_PER_CELL_VELOCITY = 1152.6
+FP64_FLOPS_PER_CELL_VELOCITY = 1120.9
 
 
 def run_gpu(args, rank, world, local_rank):

@@ -114,7 +114,8 @@ int rk_version(void);
  *                       + 8: the cell's own rows by bulk copies with mbarrier
  *                       completion in the packed kernels, same results);
  *   RYKOV_PRIO=0        no stream priorities in the graph;
- *   RYKOV_PDL=0         macro phases without programmatic serialisation;
+ *   RYKOV_PDL=1         macro phases with programmatic serialisation (default off:
+ *                       the plain launches overlap better with the micro flux);
  *   RYKOV_PACKED=0      RK_MIXED per-velocity kernels with scalar FP32 arithmetic
  *                       instead of packed FP32 pairs (rounding-level differences);
  *   RYKOV_MACRO_LANES=L threads per cell of the FP32 macro phases, 1, 2 or 4 (default

@@ -39,7 +39,9 @@ extern "C" int rk_create(rk_ctx** out, int precision, uintptr_t cuda_stream) {
     // RK_MACRO_FP32 flag: mixed contexts solve the macro PR-SGS in FP32 in delta form
     // instead of FP64 (FP64 contexts ignore it)
     ctx->use_macro32 = (precision & RK_MACRO_FP32) != 0;
-    // RYKOV_PDL=0: the macro phases as plain launches (same results)
+    // RYKOV_PDL=1: the macro phases with programmatic stream serialisation (same
+    // results; off by default: in the graph the plain launches leave the micro-flux
+    // branch beside them more room)
     if (const char* v = std::getenv("RYKOV_PDL")) ctx->use_pdl = std::strcmp(v, "0") != 0;
     // RYKOV_PACKED=0: the mixed-precision kernels with scalar FP32 arithmetic instead of
     // the packed pairs (same steps, rounding-level differences)

@@ -84,7 +84,7 @@ struct rk_ctx {
     int use_staged = RK_STAGED_DEFAULT;   // staged micro sweeps, bit mask (RYKOV_STAGED)
     bool use_prio = true;                 // stream priorities for the graph branches (RYKOV_PRIO)
     bool use_macro32 = false;             // FP32 delta-form macro PR-SGS in mixed contexts
-    bool use_pdl = true;                  // its phases with programmatic serialisation (RYKOV_PDL)
+    bool use_pdl = false;                 // its phases with programmatic serialisation (RYKOV_PDL=1)
     bool use_packed = true;               // mixed kernels on the packed FP32 pipe (RYKOV_PACKED)
     cudaStream_t cap = nullptr, cap2 = nullptr;   // capture streams (main, side branch)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bnd = nullptr, ev_int = nullptr;

@@ -44,7 +44,7 @@ struct Sched {
                                     // bit 0 first sweep, bit 1 middle sweeps, bit 2 last;
                                     // bit 3: the cell's own rows by bulk copies (packed)
     int macro32 = 0;                // macro PR-SGS in FP32 delta form (mixed contexts)
-    int pdl = 1;                    // its colour phases launched with programmatic
+    int pdl = 0;                    // its colour phases launched with programmatic
                                     // stream serialisation
     int macro_lanes = 4;            // threads per cell of the FP32 macro phases (1, 2, 4)
 };

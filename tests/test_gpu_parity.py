@@ -380,13 +380,13 @@ def test_invalid_inputs_are_rejected():
 
 @pytest.mark.parametrize("prec,env,m32", [("fp64", {"RYKOV_COOP": "1"}, False),
                                           ("fp64", {"RYKOV_GRAPH": "0"}, False),
-                                          ("fp64", {"RYKOV_PDL": "0"}, False),
-                                          ("mixed", {"RYKOV_PDL": "0"}, False),
+                                          ("fp64", {"RYKOV_PDL": "1"}, False),
+                                          ("mixed", {"RYKOV_PDL": "1"}, False),
                                           ("mixed", {"RYKOV_GRAPH": "0"}, False),
                                           ("mixed", {"RYKOV_COOP": "1"}, False),
                                           ("mixed", {"RYKOV_GRAPH": "0"}, True),
-                                          ("mixed", {"RYKOV_PDL": "0"}, True),
-                                          ("mixed", {"RYKOV_PDL": "0", "RYKOV_GRAPH": "0"}, True)])
+                                          ("mixed", {"RYKOV_PDL": "1"}, True),
+                                          ("mixed", {"RYKOV_PDL": "1", "RYKOV_GRAPH": "0"}, True)])
 def test_launch_schemes_give_identical_results(prec, env, m32, monkeypatch):
     """The cooperative macro solve (one launch, grid barriers between colours), the
     CUDA graph of an iteration and the programmatic serialisation of the FP32 macro
