@@ -45,8 +45,8 @@ CPU_STRIDE = {"scale": 50, "sphere": 30}
 # as they stand, mixed precision, from one full-size ncu capture of one second-order
 # iteration of each workload (one pass; the micro sweeps: the 16 launches' total / 16);
 # a kernel changed since the capture has no entry
-NCU_TRAFFIC = {"scale": {"k_micro_sweep": 36.20e9, "k_recon": 111.03e9, "k_face_interior": 189.69e9},
-               "sphere": {"k_micro_sweep": 1.694e9, "k_recon": 4.978e9, "k_face_interior": 6.791e9}}
+NCU_TRAFFIC = {"scale": {"k_micro_sweep": 36.20e9, "k_recon": 110.84e9, "k_face_interior": 189.67e9},
+               "sphere": {"k_micro_sweep": 1.694e9, "k_face_interior": 6.791e9}}
 
 
 def _peaks():

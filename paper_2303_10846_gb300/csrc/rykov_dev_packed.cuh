@@ -61,11 +61,35 @@ __device__ __forceinline__ void eval_eq2(const float* e, float2 ux, float2 uy, f
 // lane, the limiter's two candidate quotients formed without branches); u.n of the
 // upwind choice is rounded product by product, as in the scalar kernels.
 // ------------------------------------------------------------------------------------
+// Two blocks of eight warps per SM (up to 128 registers) with the face loops taken in
+// pairs: measured at scale 41.6 ms against 41.9 ms for three blocks with single faces
+// (paired loops spill at three blocks: 43.3 ms; single faces at two blocks: 46.1 ms)
 #ifndef RECONP_MINB
-#define RECONP_MINB 3
+#define RECONP_MINB 2
 #endif
 __device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 __device__ __forceinline__ float2 min2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+// three-input max / min (PTX max.f32 / min.f32 with three sources, sm_100+): two
+// faces' values folded into a running extreme per instruction
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float2 max3_2(float2 a, float2 b, float2 c) {
+    return make_float2(max3f(a.x, b.x, c.x), max3f(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 min3_2(float2 a, float2 b, float2 c) {
+    return make_float2(min3f(a.x, b.x, c.x), min3f(a.y, b.y, c.y));
+}
+#ifndef RECONP_PAIRS
+#define RECONP_PAIRS 3       // bit 0: limiter loop, bit 1: neighbour loop over face pairs
+#endif
 // the limiter's quotient a/b (b > 0 where it is used): approximate division, with
 // both operands scaled by 2^64 where b < 1e-30 (the approximate reciprocal overflows
 // below ~1e-38)
@@ -79,6 +103,7 @@ __global__ void __launch_bounds__(WPB * 32, RECONP_MINB) k_recon_p(Dev<float> c)
     __shared__ float4 s_B[WPB][MAXF];             // x_f - x_i, s_ij
     __shared__ float4 s_C[WPB][MAXF];             // face normal
     __shared__ int4 s_I[WPB][MAXF];               // neighbour, face, left side
+    __shared__ int2 s_J[WPB][MAXF];               // slots with a neighbour: (neighbour, slot)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * WPB + w;
     if (i >= c.N) return;                         // whole warp
@@ -91,6 +116,11 @@ __global__ void __launch_bounds__(WPB * 32, RECONP_MINB) k_recon_p(Dev<float> c)
         s_C[w][lane] = make_float4(c.slot_nT[m], c.slot_nT[c.nnz + m], c.slot_nT[2 * c.nnz + m], 0.f);
         s_I[w][lane] = make_int4(c.slot_nbr[m], c.slot_face[m], c.slot_left[m], 0);
     }
+    // the slots with a neighbour cell, in slot order: (neighbour, slot)
+    const bool hasn = lane < ns && c.slot_nbr[s0 + lane] >= 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, hasn);
+    const int nn = __popc(bal);
+    if (hasn) s_J[w][__popc(bal & ((1u << lane) - 1u))] = make_int2(c.slot_nbr[s0 + lane], lane);
     __syncwarp();
     const float eps2 = (float)c.eps2[i];
     const int limiter = (int)c.iterp[1];
@@ -109,13 +139,38 @@ __global__ void __launch_bounds__(WPB * 32, RECONP_MINB) k_recon_p(Dev<float> c)
                 g[fd][0][p] = g[fd][1][p] = g[fd][2][p] = f2(0.f);
                 dmax[fd][p] = dmin[fd][p] = f2(0.f);
             }
+        // gradient sums in slot order; Delta_max/min over the neighbours (exact, any order)
+        int qn = 0;
+        if (RECONP_PAIRS & 2) {
 #pragma unroll 1
-        for (int q = 0; q < ns; ++q) {
-            const int j = s_I[w][q].x;
-            if (j < 0) continue;
-            const float4 xg4 = *reinterpret_cast<const float4*>(c.phi + (size_t)j * c.Kp + k0);
-            const float4 xh4 = *reinterpret_cast<const float4*>(c.phi + NK + (size_t)j * c.Kp + k0);
-            const float4 A = s_A[w][q];
+            for (; qn + 1 < nn; qn += 2) {
+                const int2 J0 = s_J[w][qn], J1 = s_J[w][qn + 1];
+                const float4 xg0 = *reinterpret_cast<const float4*>(c.phi + (size_t)J0.x * c.Kp + k0);
+                const float4 xh0 = *reinterpret_cast<const float4*>(c.phi + NK + (size_t)J0.x * c.Kp + k0);
+                const float4 xg1 = *reinterpret_cast<const float4*>(c.phi + (size_t)J1.x * c.Kp + k0);
+                const float4 xh1 = *reinterpret_cast<const float4*>(c.phi + NK + (size_t)J1.x * c.Kp + k0);
+                const float4 A0 = s_A[w][J0.y], A1 = s_A[w][J1.y];
+#pragma unroll
+                for (int fd = 0; fd < 2; ++fd)
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const float4 x0 = fd ? xh0 : xg0, x1 = fd ? xh1 : xg1;
+                        const float2 d0 = sub2(p ? hi2(x0) : lo2(x0), pv[fd][p]);
+                        const float2 d1 = sub2(p ? hi2(x1) : lo2(x1), pv[fd][p]);
+                        g[fd][0][p] = fma2(f2(A1.x), d1, fma2(f2(A0.x), d0, g[fd][0][p]));
+                        g[fd][1][p] = fma2(f2(A1.y), d1, fma2(f2(A0.y), d0, g[fd][1][p]));
+                        g[fd][2][p] = fma2(f2(A1.z), d1, fma2(f2(A0.z), d0, g[fd][2][p]));
+                        dmax[fd][p] = max3_2(dmax[fd][p], d0, d1);
+                        dmin[fd][p] = min3_2(dmin[fd][p], d0, d1);
+                    }
+            }
+        }
+#pragma unroll 1
+        for (; qn < nn; ++qn) {
+            const int2 J = s_J[w][qn];
+            const float4 xg4 = *reinterpret_cast<const float4*>(c.phi + (size_t)J.x * c.Kp + k0);
+            const float4 xh4 = *reinterpret_cast<const float4*>(c.phi + NK + (size_t)J.x * c.Kp + k0);
+            const float4 A = s_A[w][J.y];
             const float2 Ax = f2(A.x), Ay = f2(A.y), Az = f2(A.z);
 #pragma unroll
             for (int fd = 0; fd < 2; ++fd)
@@ -150,9 +205,25 @@ __global__ void __launch_bounds__(WPB * 32, RECONP_MINB) k_recon_p(Dev<float> c)
             for (int fd = 0; fd < 2; ++fd)
 #pragma unroll
                 for (int p = 0; p < 2; ++p) d2hi[fd][p] = d2lo[fd][p] = f2(0.f);
+            int qb = 0;
+            if (RECONP_PAIRS & 1) {
 #pragma unroll 1
-            for (int q = 0; q < ns; ++q) {
-                const float4 B = s_B[w][q];
+                for (; qb + 1 < ns; qb += 2) {
+                    const float4 B0 = s_B[w][qb], B1 = s_B[w][qb + 1];
+#pragma unroll
+                    for (int fd = 0; fd < 2; ++fd)
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            const float2 e0 = fma2(g[fd][2][p], f2(B0.z), fma2(g[fd][1][p], f2(B0.y), mul2(g[fd][0][p], f2(B0.x))));
+                            const float2 e1 = fma2(g[fd][2][p], f2(B1.z), fma2(g[fd][1][p], f2(B1.y), mul2(g[fd][0][p], f2(B1.x))));
+                            d2hi[fd][p] = max3_2(d2hi[fd][p], e0, e1);
+                            d2lo[fd][p] = min3_2(d2lo[fd][p], e0, e1);
+                        }
+                }
+            }
+#pragma unroll 1
+            for (; qb < ns; ++qb) {
+                const float4 B = s_B[w][qb];
                 const float2 Bx = f2(B.x), By = f2(B.y), Bz = f2(B.z);
 #pragma unroll
                 for (int fd = 0; fd < 2; ++fd)
