@@ -195,22 +195,25 @@ def cpu_sample_desc(wl, sample_k, stride, what):
 def oracle_table(steps=2):
     """The CPU-baseline plan's table: the oracle's time per iteration on one core and
     on all cores for the cavity (512 cells x 512 velocities, whole case) and the
-    sphere (every 10th velocity), each in a child process with OMP_NUM_THREADS set."""
+    sphere (every 10th velocity), and on all cores for the capsule (every 20th
+    velocity, 5 timed iterations), each in a child process with OMP_NUM_THREADS set."""
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
             "from paper_2303_10846_gb300 import inputs as I; "
-            "wl = I.cavity_workload() if sys.argv[1] == 'cavity' else "
-            "bench.dvs_sample(I.sphere_workload(), 10); "
-            "v, dt = bench.oracle_rate(wl, %d, 1); "
-            "print(json.dumps({'updates_per_s': v, 's_per_iteration': dt / %d, "
-            "'N': wl.mesh.n_cell, 'K': wl.dvs.K}))" % (ROOT, steps, steps))
+            "c, n = sys.argv[1], int(sys.argv[2]); "
+            "wl = I.cavity_workload() if c == 'cavity' else "
+            "bench.dvs_sample(I.sphere_workload(), 10) if c == 'sphere' else "
+            "bench.dvs_sample(I.capsule_workload(), 20); "
+            "v, dt = bench.oracle_rate(wl, n, 1); "
+            "print(json.dumps({'updates_per_s': v, 's_per_iteration': dt / n, "
+            "'iterations': n, 'N': wl.mesh.n_cell, 'K': wl.dvs.K}))" % ROOT)
     out = {}
-    for case in ("cavity", "sphere"):
-        for threads in (1, _cores()):
-            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
-            r = subprocess.run([sys.executable, "-c", code, case], capture_output=True, text=True,
-                               env=env, timeout=900)
-            line = [l for l in r.stdout.splitlines() if l.startswith("{")]
-            out[f"{case}_threads{threads}"] = json.loads(line[-1]) if line else {"error": r.stderr[-300:]}
+    for case, threads, n in (("cavity", 1, steps), ("cavity", _cores(), steps), ("sphere", 1, steps),
+                             ("sphere", _cores(), steps), ("capsule", _cores(), 5)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, "-c", code, case, str(n)], capture_output=True, text=True,
+                           env=env, timeout=900)
+        line = [l for l in r.stdout.splitlines() if l.startswith("{")]
+        out[f"{case}_threads{threads}"] = json.loads(line[-1]) if line else {"error": r.stderr[-300:]}
     return out
 
 
