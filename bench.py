@@ -193,7 +193,7 @@ def cpu_sample_desc(wl, sample_k, stride, what):
 
 
 def oracle_table(steps=2):
-    """The CPU-baseline plan's table: the oracle's time per iteration on one core and
+    """The oracle's timing table: its time per iteration on one core and
     on all cores for the cavity (512 cells x 512 velocities, whole case) and the
     sphere (every 10th velocity), and on all cores for the capsule (every 20th
     velocity, 5 timed iterations), each in a child process with OMP_NUM_THREADS set."""

@@ -813,7 +813,8 @@ __global__ void __launch_bounds__(WPB * 32, sizeof(T) == 8 ? 4 : RECON_MINB) k_r
                 vload(c.lstore + NK + (size_t)i * c.Kp + k0, L[1]);
             } else if (limiter == 1 || limiter == 4) {
                 // min over faces of Venkatakrishnan's psi(d1, d2), capped at 1, threshold
-                // eps^2 phi_i^2 relative to the cell value (readings).  psi < 1 needs
+                // eps^2 phi_i^2 relative to the cell value (unlike the published absolute
+                // eps^2, which diverged on the sphere).  psi < 1 needs
                 // y = d2/d1 > 1/2, where psi decreases in y; so the minimum over the faces
                 // with d2 > 0 is psi(Delta_max, max d2) and over d2 < 0 psi(Delta_min, min d2):
                 // two evaluations instead of one per face (the same value up to rounding)
@@ -1298,7 +1299,8 @@ __device__ __forceinline__ bool flux_prim(const double* W, double* P) {
 // primitives of W^n; dW~ = 0.
 // implicit-step factor and reconstruction order of the current iteration:
 // cfl = min(cfl_imp, cfl_imp0 cfl_ramp^n) (cfl_imp if no ramp), first order for
-// n < first_order_iters (readings of the unspecified implicit step and start-up)
+// n < first_order_iters (the paper fixes neither the implicit step nor a start-up:
+// both are parameters of this implementation)
 template <typename T>
 __global__ void k_iter_begin(Dev<T> c) {
     const double n = c.iterp[2];

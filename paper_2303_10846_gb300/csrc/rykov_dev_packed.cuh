@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(WPB * 32, RECONP_MINB) k_recon_p(Dev<float> c)
             L[0][0] = lo2(l0); L[0][1] = hi2(l0); L[1][0] = lo2(l1); L[1][1] = hi2(l1);
         } else if (limiter == 1 || limiter == 4) {
             // min over faces of Venkatakrishnan's psi(d1, d2), capped at 1, threshold
-            // eps^2 phi_i^2 (readings); with d2 the gradient change to each face
+            // eps^2 phi_i^2 (relative to the cell value, unlike the published absolute
+            // eps^2, which diverged on the sphere); with d2 the gradient change to each face
             // centroid, psi < 1 needs d2/d1 > 1/2 where psi decreases in d2/d1, so the
             // minimum is psi(Delta_max, max d2) over d2 > 0 and psi(Delta_min, min d2)
             // over d2 < 0

@@ -235,7 +235,7 @@ def test_scale_case_sampled():
 
 
 def test_mixed_matches_fp64_on_the_surface_at_full_size(sphere):
-    """North-star accuracy target of the mixed form: wall pressure, heat flux and drag
+    """Accuracy target of the mixed form: wall pressure, heat flux and drag
     within 1e-5 (relative to their largest values) of the FP64 form after the same
     iterations from the same state."""
     s64 = _solver(sphere, "fp64")
